@@ -292,43 +292,47 @@ typedef struct {
 
 static int cell_brute(work_t* W, int64_t i, int64_t N, const double* pos, const double* psi,
                       const double* L, double dpsi_max) {
-    int64_t nc = 0;
     const double* yi = pos + 3 * i;
-    for (int64_t j = 0; j < N; j++) {
-        double m[3];
-        for (int e = 0; e < 3; e++) m[e] = wrap1(pos[3 * j + e] - yi[e], L[e]);
-        for (int s = 0; s < 27; s++) {
-            int sx = s % 3 - 1, sy = (s / 3) % 3 - 1, sz = s / 9 - 1;
-            if (j == i && sx == 0 && sy == 0 && sz == 0) continue;
-            cand_t* c = &W->cand[nc++];
-            c->d[0] = m[0] + sx * L[0];
-            c->d[1] = m[1] + sy * L[1];
-            c->d[2] = m[2] + sz * L[2];
-            c->d2 = dot3(c->d, c->d);
-            c->j = j;
-        }
-    }
-    qsort(W->cand, nc, sizeof(cand_t), cmp_cand);
+    double Lmin = fmin(L[0], fmin(L[1], L[2]));
     poly_box(&W->P, L);
     double R = poly_radius(&W->P);
-    for (int64_t c = 0; c < nc; c++) {
-        const cand_t* k = &W->cand[c];
-        if (k->j == i) {
-            /* own image: psi difference is zero; the box faces already are these
-               planes for the six face images, the rest are tested like others */
-            if (clip_cand(&W->P, &W->Q, W->cap, k->d, -1, 0.0, 0.0, &R) == OR_OVERFLOW)
-                return OR_OVERFLOW;
-        } else if (clip_cand(&W->P, &W->Q, W->cap, k->d, k->j, psi[i], psi[k->j], &R) ==
-                   OR_OVERFLOW) {
-            return OR_OVERFLOW;
+    /* shells of image shifts: shell s holds the shifts with max|shift| == s; every
+       image outside shells 0..s lies at |d| >= (s + 1/2) min(L) */
+    for (int sh = 1; sh <= 4; sh++) {
+        int64_t nc = 0;
+        int w = 2 * sh + 1;
+        for (int64_t j = 0; j < N; j++) {
+            double m[3];
+            for (int e = 0; e < 3; e++) m[e] = wrap1(pos[3 * j + e] - yi[e], L[e]);
+            for (int s = 0; s < w * w * w; s++) {
+                int sx = s % w - sh, sy = (s / w) % w - sh, sz = s / (w * w) - sh;
+                int cheb = abs(sx) > abs(sy) ? abs(sx) : abs(sy);
+                if (abs(sz) > cheb) cheb = abs(sz);
+                if (sh == 1 ? cheb > 1 : cheb != sh) continue;
+                if (j == i && cheb == 0) continue;
+                if (nc >= W->ncand_cap) return OR_OVERFLOW;
+                cand_t* c = &W->cand[nc++];
+                c->d[0] = m[0] + sx * L[0];
+                c->d[1] = m[1] + sy * L[1];
+                c->d[2] = m[2] + sz * L[2];
+                c->d2 = dot3(c->d, c->d);
+                c->j = j;
+            }
         }
-        if (W->P.nf == 0) return OR_EMPTY;
+        qsort(W->cand, nc, sizeof(cand_t), cmp_cand);
+        for (int64_t c = 0; c < nc; c++) {
+            const cand_t* k = &W->cand[c];
+            /* own images have a zero psi difference; the six face images are the
+               box faces already, the others are clipped like any plane */
+            int64_t tag = (k->j == i) ? -1 : k->j;
+            double pj = (k->j == i) ? psi[i] : psi[k->j];
+            if (clip_cand(&W->P, &W->Q, W->cap, k->d, tag, psi[i], pj, &R) == OR_OVERFLOW)
+                return OR_OVERFLOW;
+            if (W->P.nf == 0) return OR_EMPTY;
+        }
+        if (R + sqrt(R * R + 2.0 * dpsi_max) <= (sh + 0.5) * Lmin) return OR_OK;
     }
-    /* images outside the 27 shifts lie at |d| >= 1.5 min(L) */
-    double Lmin = fmin(L[0], fmin(L[1], L[2]));
-    double need = R + sqrt(R * R + 2.0 * dpsi_max);
-    if (need > 1.5 * Lmin) return OR_NOT_CERTIFIED;
-    return OR_OK;
+    return OR_NOT_CERTIFIED;
 }
 
 static int cell_certified(work_t* W, int64_t i, int64_t N, const double* pos,
@@ -373,9 +377,12 @@ static int one_cell(work_t* W, int64_t i, int64_t N, const double* pos, const do
     int st;
     if (mode == 1) st = cell_certified(W, i, N, pos, psi, L, dpsi);
     if (mode != 1 || st == OR_NOT_CERTIFIED) {
-        if (W->ncand_cap < 27 * N) {
+        /* brute force is only meant for small N (the largest image shell holds
+           9^3 - 7^3 = 386 shifts per seed) */
+        if (N > 200000) return OR_NOT_CERTIFIED;
+        if (W->ncand_cap < 386 * N) {
             free(W->cand);
-            W->ncand_cap = 27 * N;
+            W->ncand_cap = 386 * N;
             W->cand = (cand_t*)malloc(sizeof(cand_t) * (size_t)W->ncand_cap);
         }
         st = cell_brute(W, i, N, pos, psi, L, dpsi);
@@ -416,7 +423,7 @@ int oracle_cells(int64_t N, const double* pos, const double* psi, const double* 
     for (int64_t j = 0; j < N; j++)
         if (psi[j] > psi_max) psi_max = psi[j];
     int agg = 0;
-    int64_t cand_cap = (mode == 1 ? N : 27 * N);
+    int64_t cand_cap = (mode == 1 ? N : 386 * N);
 #pragma omp parallel reduction(| : agg)
     {
         work_t* W = (work_t*)malloc(sizeof(work_t));

@@ -92,7 +92,7 @@ def zeldovich_box(n, L, spectrum, rms, seed):
     comps = []
     for kc in (kx, ky, kz):
         sk = 1j * kc * inv_k2 * dk
-        comps.append(np.fft.irfftn(sk, s=(n, n, n)))
+        comps.append(np.fft.irfftn(sk, s=(n, n, n), axes=(0, 1, 2)))
     # array index order is (z, y, x); flatten to match lattice() (x fastest)
     s = np.stack([c.ravel() for c in comps], axis=1)
     cur = np.sqrt(np.mean(np.sum(s * s, axis=1)))

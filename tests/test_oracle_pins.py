@@ -1,0 +1,271 @@
+"""Pins for the CPU oracle against facts fixed by the mathematics (no GPU).
+
+The paper (arXiv:2110.08868) prints no worked example, so the oracle is pinned by
+closed forms (lattice, translated lattice, two-seed slab, separable plane wave),
+brute force, finite differences of K (eq. SDK), invariants of the Laguerre
+diagram (eq. laguerrecell), an independent point-location estimate and a
+library kNN.
+"""
+import numpy as np
+import pytest
+from scipy.spatial import cKDTree
+
+import sdot_oracle as O
+from paper_2110_08868_gb300 import ics
+
+
+def _lattice_expect(n, L):
+    a = L / n
+    return a, a ** 3
+
+
+@pytest.mark.parametrize("n", [4, 5])
+@pytest.mark.parametrize("mode", ["brute", "certified"])
+def test_lattice_cubes(n, mode):
+    # psi = 0 on a lattice: every cell is the cube of side a around its seed;
+    # facets are the 6 face neighbours with area a^2 at distance a, so
+    # L = a * (7-point Laplacian); K = N a^5 / 8 (int over cube of 1/2|p|^2).
+    L = 1.0
+    q = ics.lattice(n, L)
+    N = n ** 3
+    a, v = _lattice_expect(n, L)
+    nu = ics.uniform_masses(N, L)
+    ev = O.laguerre(q, np.zeros(N), L, nu, mode=mode)
+    np.testing.assert_allclose(ev["vol"], v, rtol=1e-13)
+    np.testing.assert_allclose(ev["local_centroid"], 0.0, atol=1e-14)
+    assert abs(ev["K"] - N * a ** 5 / 8) < 1e-13 * N * a ** 5
+    Lm = ev["L"].toarray()
+    np.testing.assert_allclose(np.diag(Lm), 6 * a, rtol=1e-13)
+    off = Lm - np.diag(np.diag(Lm))
+    # each row: exactly 6 entries equal to -a (n >= 3 so the 6 are distinct)
+    for i in range(N):
+        nz = off[i][np.abs(off[i]) > 1e-12 * a]
+        assert nz.size == 6
+        np.testing.assert_allclose(nz, -a, rtol=1e-12)
+    np.testing.assert_allclose(O.displacement(ev), 0.0, atol=1e-14)
+
+
+def test_translated_lattice():
+    # y = q + t: psi = 0 already balances the masses; cells are cubes centred on
+    # the seeds, so the displacement is 0 (a uniform shift is invisible on a torus).
+    n, L = 4, 1.0
+    t = np.array([0.013, -0.071, 0.2])
+    y = np.mod(ics.lattice(n, L) + t, L)
+    N = n ** 3
+    ev = O.laguerre(y, np.zeros(N), L, ics.uniform_masses(N, L))
+    np.testing.assert_allclose(ev["vol"], (L / n) ** 3, rtol=1e-13)
+    np.testing.assert_allclose(O.displacement(ev), 0.0, atol=1e-14)
+
+
+@pytest.mark.parametrize("delta", [0.0, 0.01, -0.03])
+def test_two_seed_slab(delta):
+    # seeds (1/4,1/2,1/2) and (3/4,1/2,1/2), psi = (delta, 0): the two facets with the
+    # images of seed 2 at x = 1/4 + 1/4 + 2 delta and x = 1/4 - 1/4 - 2 delta, so
+    # V_1 = 1/2 + 4 delta; each facet has area 1 and |d| = 1/2, so L_12 = -4.
+    y = np.array([[0.25, 0.5, 0.5], [0.75, 0.5, 0.5]])
+    psi = np.array([delta, 0.0])
+    for mode in ("brute", "certified"):
+        ev = O.laguerre(y, psi, 1.0, np.array([0.5, 0.5]), mode=mode)
+        assert abs(ev["vol"][0] - (0.5 + 4 * delta)) < 1e-14
+        assert abs(ev["vol"][1] - (0.5 - 4 * delta)) < 1e-14
+        Lm = ev["L"].toarray()
+        assert abs(Lm[0, 1] + 4.0) < 1e-13 and abs(Lm[1, 0] + 4.0) < 1e-13
+        assert abs(Lm[0, 0] - 4.0) < 1e-13
+
+
+def plane_wave(n, L, amps, phases):
+    """Separable displacement s_a(q_a) = A_a sin(2 pi q_a / L + phi_a) and its exact psi.
+
+    With 1 + s' > 0 (no shell crossing) and zero lattice mean, the power distance
+    separates per axis and every Laguerre cell is the lattice cube of its seed. The
+    1D weights follow from equal power at the cube face p = q_m + a/2:
+      psi_{m+1} - psi_m = 1/2 D^2 - D (p - x_m),  D = x_{m+1} - x_m (unwrapped).
+    """
+    a = L / n
+    g = (np.arange(n) + 0.5) * a
+    psis, xs = [], []
+    for A, ph in zip(amps, phases):
+        assert 2 * np.pi * A / L < 1
+        x = g + A * np.sin(2 * np.pi * g / L + ph)
+        xn = np.append(x, x[0] + L)
+        p = g + 0.5 * a
+        D = np.diff(xn)
+        inc = 0.5 * D ** 2 - D * (p - x)
+        assert abs(inc.sum()) < 1e-12 * L * L  # closes around the torus
+        psis.append(np.concatenate([[0.0], np.cumsum(inc[:-1])]))
+        xs.append(x)
+    iz, iy, ix = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    ix, iy, iz = ix.ravel(), iy.ravel(), iz.ravel()
+    y = np.stack([xs[0][ix], xs[1][iy], xs[2][iz]], axis=1)
+    psi = psis[0][ix] + psis[1][iy] + psis[2][iz]
+    s = y - ics.lattice(n, L)
+    return np.mod(y, L), psi - psi.mean(), s
+
+
+def test_plane_wave_closed_form_cells():
+    n, L = 6, 1.0
+    y, psi, s = plane_wave(n, L, [0.09, 0.05, 0.12], [0.3, 1.1, -0.4])
+    N = n ** 3
+    ev = O.laguerre(y, psi, L, ics.uniform_masses(N, L))
+    np.testing.assert_allclose(ev["vol"], (L / n) ** 3, rtol=1e-11)
+    np.testing.assert_allclose(O.displacement(ev), s, atol=1e-11 * L / n)
+
+
+def test_plane_wave_newton_recovers_closed_form():
+    n, L = 6, 1.0
+    y, psi_exact, s = plane_wave(n, L, [0.09, 0.05, 0.12], [0.3, 1.1, -0.4])
+    N = n ** 3
+    nu = ics.uniform_masses(N, L)
+    psi, info = O.solve(y, nu, L, tol=1e-12)
+    a = L / n
+    np.testing.assert_allclose(psi, psi_exact, atol=1e-9 * a * a)
+    np.testing.assert_allclose(info["disp"], s, atol=1e-9 * a)
+
+
+def _random_case(n=5, L=1.0, rms=0.3, seed=7, psi_scale=0.01):
+    y, _, _ = ics.zeldovich_box(n, L, ics.spectrum_kinv, rms, seed)
+    a = L / n
+    rng = np.random.default_rng(seed + 1)
+    psi = psi_scale * a * a * rng.standard_normal(y.shape[0])
+    return y, psi, L
+
+
+def test_brute_equals_certified():
+    for seed in (3, 4):
+        y, psi, L = _random_case(n=6, seed=seed)
+        b = O.cells(y, psi, L, "brute")
+        c = O.cells(y, psi, L, "certified")
+        np.testing.assert_allclose(b["vol"], c["vol"], rtol=1e-12, atol=0)
+        np.testing.assert_allclose(b["m1"], c["m1"], atol=1e-15)
+        Lb = O.hessian_laplacian(b, y.shape[0]).toarray()
+        Lc = O.hessian_laplacian(c, y.shape[0]).toarray()
+        np.testing.assert_allclose(Lb, Lc, atol=1e-12 * np.abs(Lb).max())
+
+
+def test_invariants():
+    y, psi, L = _random_case(n=6, seed=11)
+    N = y.shape[0]
+    nu = ics.uniform_masses(N, L)
+    ev = O.laguerre(y, psi, L, nu)
+    assert ev["vol"].min() > 0.01 * nu[0]  # no empty cell
+    # volumes tile the box
+    assert abs(ev["vol"].sum() - L ** 3) < 1e-12 * L ** 3
+    Lm = ev["L"].toarray()
+    # symmetric, zero row sums, positive semi-definite with a 1-D kernel
+    np.testing.assert_allclose(Lm, Lm.T, atol=1e-12 * np.abs(Lm).max())
+    np.testing.assert_allclose(Lm.sum(axis=1), 0.0, atol=1e-12 * np.abs(Lm).max())
+    w = np.linalg.eigvalsh(Lm)
+    assert w[0] > -1e-10 * w[-1] and w[1] > 1e-8 * w[-1]
+    # psi + c changes no cell
+    ev2 = O.laguerre(y, psi + 0.123, L, nu)
+    np.testing.assert_allclose(ev2["vol"], ev["vol"], rtol=1e-12)
+    # permutation equivariance
+    perm = np.random.default_rng(0).permutation(N)
+    ev3 = O.laguerre(y[perm], psi[perm], L, nu[perm])
+    np.testing.assert_allclose(ev3["vol"], ev["vol"][perm], rtol=1e-12)
+    # translation covariance (positions shifted on the torus, same cells)
+    t = np.array([0.31, -0.17, 0.05])
+    ev4 = O.laguerre(np.mod(y + t, L), psi, L, nu)
+    np.testing.assert_allclose(ev4["vol"], ev["vol"], rtol=1e-12)
+    np.testing.assert_allclose(ev4["local_centroid"], ev["local_centroid"], atol=1e-13)
+
+
+def test_finite_differences():
+    # dK/dpsi_i = nu_i - V_i and dV_i/dpsi_j = L_ij (eq. SDK differentiated)
+    y, psi, L = _random_case(n=5, seed=21)
+    N = y.shape[0]
+    nu = ics.uniform_masses(N, L)
+    a = L / 5
+    ev = O.laguerre(y, psi, L, nu)
+    Lm = ev["L"].toarray()
+    h = 1e-6 * a * a
+    rng = np.random.default_rng(5)
+    for i in rng.choice(N, 6, replace=False):
+        e = np.zeros(N)
+        e[i] = h
+        p = O.laguerre(y, psi + e, L, nu, with_hessian=False)
+        m = O.laguerre(y, psi - e, L, nu, with_hessian=False)
+        g_fd = (p["K"] - m["K"]) / (2 * h)
+        assert abs(g_fd - ev["grad"][i]) < 1e-6 * nu[i]
+        col_fd = (p["vol"] - m["vol"]) / (2 * h)
+        np.testing.assert_allclose(col_fd, Lm[:, i], atol=1e-6 * np.abs(Lm[i, i]))
+
+
+def test_point_location_volumes_and_centroids():
+    # Independent of the polytope code: assign a fine grid of sample points to the
+    # cell minimising 1/2|q - y_j|^2 - psi_j (min image) and compare volume and
+    # centroid estimates with the clipped cells.
+    n, L = 3, 1.0
+    a = L / n
+    rng = np.random.default_rng(31)
+    y = np.mod(ics.lattice(n, L) + rng.uniform(-0.25, 0.25, (n ** 3, 3)) * a, L)
+    psi = 0.1 * a * a * rng.standard_normal(n ** 3)
+    N = y.shape[0]
+    m = 72
+    g = (np.arange(m) + 0.5) / m * L
+    Q = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    best = np.full(Q.shape[0], np.inf)
+    arg = np.zeros(Q.shape[0], dtype=np.int64)
+    off = np.zeros((Q.shape[0], 3))
+    for j in range(N):
+        d = Q - y[j]
+        d -= L * np.round(d / L)
+        pw = 0.5 * np.sum(d * d, axis=1) - psi[j]
+        better = pw < best
+        best[better] = pw[better]
+        arg[better] = j
+        off[better] = d[better]
+    ev = O.laguerre(y, psi, L)
+    cnt = np.bincount(arg, minlength=N)
+    vol_pl = cnt / Q.shape[0] * L ** 3
+    assert ev["vol"].min() > 0.1 * L ** 3 / N
+    np.testing.assert_allclose(vol_pl, ev["vol"], rtol=0.03)
+    for j in range(N):
+        cen = off[arg == j].mean(axis=0)
+        np.testing.assert_allclose(cen, ev["local_centroid"][j], atol=0.02 * L / n)
+
+
+def test_knn_against_kdtree():
+    rng = np.random.default_rng(2)
+    L = 1.0
+    y = rng.uniform(0, L, size=(700, 3))
+    k = 24
+    nb, d2 = O.knn(y, L, k)
+    tree = cKDTree(y, boxsize=L)
+    dd, ii = tree.query(y, k=k + 1)
+    np.testing.assert_array_equal(nb, ii[:, 1:])
+    np.testing.assert_allclose(np.sqrt(d2), dd[:, 1:], rtol=1e-13)
+
+
+def test_knn_lattice_tie_order():
+    # 4^3 lattice: 6 face neighbours (d^2 = a^2), then 12 edge (2a^2), 8 corner (3a^2),
+    # then the 3 half-box neighbours (d^2 = 4a^2, counted once each); ties by index.
+    n, L = 4, 1.0
+    y = ics.lattice(n, L)
+    nb, d2 = O.knn(y, L, 29)
+    for i in (0, 21, 63):
+        ix, iy, iz = i % n, (i // n) % n, i // (n * n)
+        groups = {}
+        for j in range(n ** 3):
+            if j == i:
+                continue
+            jx, jy, jz = j % n, (j // n) % n, j // (n * n)
+            dd = [min((jx - ix) % n, (ix - jx) % n), min((jy - iy) % n, (iy - jy) % n),
+                  min((jz - iz) % n, (iz - jz) % n)]
+            groups.setdefault(sum(c * c for c in dd), []).append(j)
+        expect = []
+        for key in sorted(groups):
+            expect += sorted(groups[key])
+        assert list(nb[i]) == expect[:29]
+
+
+def test_newton_c1_small_converges():
+    y, nu, L = ics.make_config(**ics.CONFIGS["zeldovich-16^3-kinv-0.3a"])
+    # a 8^3 version of the same recipe keeps the CPU suite fast
+    y, _, _ = ics.zeldovich_box(8, 1.0, ics.spectrum_kinv, 0.3, 1)
+    N = y.shape[0]
+    nu = ics.uniform_masses(N, 1.0)
+    psi, info = O.solve(y, nu, 1.0, tol=1e-10)
+    assert info["hist"][-1] <= 1e-10
+    assert abs(psi.sum()) < 1e-12
+    np.testing.assert_allclose(info["vol"], nu, rtol=1e-10)
