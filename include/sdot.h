@@ -1,0 +1,175 @@
+/*
+ * sdot.h — semi-discrete optimal transport on one GPU (sm_103a), C ABI.
+ *
+ * Problem (arXiv:2110.08868, Sec. "Monge-Ampere-Kantorovich Reconstruction"):
+ * N points y_j with masses nu_j sit in a periodic box of volume |B| = sum_j nu_j
+ * (uniform Lagrangian density rho_I = 1). The library finds the weights psi_j that
+ * maximise the semi-discrete Kantorovich dual, eq. (SDK),
+ *     K(psi) = sum_j int_{V_j} [1/2 |y_j - q|^2 - psi_j] dq + sum_j nu_j psi_j,
+ * whose Laguerre cells, eq. (laguerrecell),
+ *     V_j = { q : 1/2|y_j - q|^2 - psi_j < 1/2|y_k - q|^2 - psi_k  for all k != j },
+ * then all have volume nu_j. Distances are periodic (minimum image).
+ *
+ * Conventions for every call:
+ *  - Return value: SDOT_OK (0) or a negative SDOT_ERR_* code; sdot_last_error()
+ *    then gives a message (per calling thread).
+ *  - Vector arguments are plain pointers to host OR device memory; the library
+ *    inspects each pointer (cudaPointerGetAttributes) and copies as needed. The
+ *    caller owns every buffer it passes; nothing is retained after the call
+ *    returns, except where stated (borrowed CSR pointers).
+ *  - All index spaces are the caller's order 0..N-1.
+ *  - Work is issued on the context's stream (default: the legacy default stream;
+ *    see sdot_set_stream). Calls that return host data synchronise that stream.
+ *  - A context is not thread-safe; different contexts are independent.
+ */
+#ifndef SDOT_H
+#define SDOT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    SDOT_OK = 0,
+    SDOT_ERR_ARG = -1,        /* invalid argument (NULL, N < 2, bad option, non-finite input) */
+    SDOT_ERR_MASS = -2,       /* |sum nu - |box|| > 1e-10 |box| or a mass <= 0 */
+    SDOT_ERR_DUPLICATE = -3,  /* two seeds at the same position */
+    SDOT_ERR_TOO_FEW = -4,    /* a cell reaches half a box: too few seeds for minimum image */
+    SDOT_ERR_OOM = -5,        /* device allocation failed */
+    SDOT_ERR_NO_DESCENT = -6, /* line search step fell below alpha_min */
+    SDOT_ERR_MAXIT = -7,      /* Newton did not reach tol within newton_maxit */
+    SDOT_ERR_EMPTY_CELL = -8, /* a Laguerre cell is empty at the given psi */
+    SDOT_ERR_TIMEOUT = -9,    /* a bounded device wait gave up */
+    SDOT_ERR_CUDA = -10,      /* CUDA runtime error */
+    SDOT_ERR_CAPACITY = -11   /* a cell exceeded the fixed polytope capacity even in FP64 */
+};
+
+enum {
+    SDOT_PREC_FP64 = 0,  /* clipping in FP64 */
+    SDOT_PREC_MIXED = 1  /* clipping in FP32 in seed-local coordinates, FP64 accumulation,
+                            FP64 re-clip of cells failing the consistency check */
+};
+
+typedef struct {
+    int k;                 /* neighbours per seed in the kNN list (1..64, default 24) */
+    int precision;         /* SDOT_PREC_FP64 or SDOT_PREC_MIXED (default MIXED) */
+    double seeds_per_leaf; /* mean seeds per grid cell of the spatial hash (default 2) */
+    double cg_rtol;        /* PCG stop: ||r|| <= cg_rtol ||g|| (default 1e-3; tightened
+                              near convergence to 0.1 tol) */
+    int cg_maxit;          /* PCG iteration cap per Newton step (default 5000) */
+    int newton_maxit;      /* Newton iteration cap (default 100) */
+    double alpha_min;      /* smallest damping step before SDOT_ERR_NO_DESCENT (2^-30) */
+    int verbose;           /* 1: one JSON line per Newton iteration on stderr */
+} sdot_options;
+
+/* The Hessian in CSR form. L = -Hessian(K) is the weighted graph Laplacian
+ * L_ij = -A_ij / |d_ij| (A_ij: facet area, d_ij: min-image seed difference),
+ * L_ii = -sum_{j != i} L_ij. Device pointers, owned by the context, valid until the
+ * next sdot_laguerre / sdot_solve / sdot_destroy on it. Row i holds the diagonal
+ * first, then the off-diagonal entries in increasing column order. */
+typedef struct {
+    int64_t n;
+    int64_t nnz;
+    const int64_t* row_ptr; /* n + 1 */
+    const int32_t* col;     /* nnz */
+    const double* val;      /* nnz */
+} sdot_csr;
+
+typedef struct {
+    int newton_iters;
+    int laguerre_evals;      /* cell-diagram evaluations, line-search trials included */
+    int64_t cg_iters;        /* total PCG iterations */
+    double max_rel_err;      /* max_j |V_j - nu_j| / nu_j at return */
+    double l2_err;           /* ||V - nu||_2 at return */
+    double min_vol;          /* min_j V_j at return */
+    double last_alpha;       /* damping factor of the last step */
+    int64_t requeued;        /* cells re-queued by the security test (last evaluation) */
+    int64_t reclipped_fp64;  /* cells re-clipped in FP64 (last evaluation) */
+    double ms_knn;           /* device time of the kNN build (sdot_create) */
+    double ms_clip;          /* device time in cell clipping (all evaluations) */
+    double ms_cg;            /* device time in PCG */
+    double ms_total;         /* wall time of the solve */
+} sdot_stats;
+
+typedef struct sdot_ctx sdot_ctx;
+
+/* Fill *opt with the defaults listed in sdot_options. */
+int sdot_default_options(sdot_options* opt);
+
+/*
+ * Create a context for N seeds and build the grid hash and the kNN lists.
+ *  pos:  N x 3 doubles, row-major (x, y, z); every coordinate in [0, box[a]).
+ *  mass: N doubles, each > 0, summing to box[0]*box[1]*box[2] within 1e-10
+ *        relative (eq. SDK with rho_I = 1); NULL means uniform |box| / N.
+ *  box:  3 box lengths (host memory).
+ *  opt:  NULL for defaults. Copied.
+ * The seeds are sorted internally by grid cell; results are returned in the
+ * caller's order. On error *out is NULL.
+ */
+int sdot_create(const double* pos, const double* mass, int64_t N, const double box[3],
+                const sdot_options* opt, sdot_ctx** out);
+
+/* Issue all later work of ctx on this cudaStream_t (NULL: legacy default stream). */
+int sdot_set_stream(sdot_ctx* ctx, void* stream);
+
+/*
+ * One evaluation of the Laguerre diagram at psi (eq. laguerrecell) with the
+ * quantities of eq. (SDK) and its derivatives.
+ *  psi:       N doubles, or NULL for the context's current psi (0 after create).
+ *             A non-NULL psi also becomes the current psi.
+ *  volumes:   N doubles out (|V_j|) or NULL.
+ *  centroids: N x 3 doubles out (absolute, wrapped into the box) or NULL.
+ *  hess:      out, L = -Hessian(K) in the caller's index order, or NULL.
+ * Returns SDOT_ERR_EMPTY_CELL (outputs still written) if some cell is empty.
+ */
+int sdot_laguerre(sdot_ctx* ctx, const double* psi, double* volumes, double* centroids,
+                  sdot_csr* hess);
+
+/*
+ * Damped Newton maximisation of K (concave and C^2, Sec. "Monge-Ampere-Kantorovich
+ * Reconstruction") from psi0 (N doubles; NULL: 0) until
+ * max_j |V_j - nu_j| / nu_j <= tol. Each step solves L delta = nu - V by
+ * Jacobi-preconditioned CG and takes the first alpha in 1, 1/2, 1/4, ... with
+ * min_j V_j >= eps0 and ||nu - V||_2 <= (1 - alpha/2) ||nu - V(psi)||_2, where
+ * eps0 = 1/2 min(min_j V_j(psi0), min_j nu_j). The result keeps sum(psi) = 0.
+ * st may be NULL.
+ */
+int sdot_solve(sdot_ctx* ctx, double tol, const double* psi0, sdot_stats* st);
+
+/* Copy a CSR returned by sdot_laguerre into caller buffers (host or device):
+ * row_ptr n + 1 int64, col nnz int32, val nnz doubles. */
+int sdot_csr_copy(const sdot_csr* h, int64_t* row_ptr, int32_t* col, double* val);
+
+/* Current psi (N doubles out, sum zero after a solve). */
+int sdot_get_psi(sdot_ctx* ctx, double* psi);
+
+/*
+ * Displacement of every cell at the current psi: disp_j = y_j - centroid(V_j),
+ * minimum image (N x 3 doubles out). Each cell is mapped to its point (last
+ * paragraph of Sec. "Monge-Ampere-Kantorovich Reconstruction"); this is the
+ * Zel'dovich displacement of that mass element.
+ */
+int sdot_displacement(sdot_ctx* ctx, double* disp);
+
+/* The kNN lists built by sdot_create: N x k int32 out, neighbours of seed j in
+ * increasing (min-image d^2, index) order, d^2 = (dx*dx + dy*dy) + dz*dz in IEEE
+ * binary64 without fused multiply-add. */
+int sdot_knn(sdot_ctx* ctx, int32_t* nbr);
+
+/* Number of seeds and kNN size of the context. */
+int sdot_size(const sdot_ctx* ctx, int64_t* N, int* k);
+
+/* Release every resource of ctx (NULL is accepted). */
+void sdot_destroy(sdot_ctx* ctx);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* sdot_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SDOT_H */

@@ -1,0 +1,255 @@
+"""Thin ctypes binding of libsdot (include/sdot.h): argument marshalling only.
+
+Every function keeps the C name and returns the C status code; the buffers may be
+numpy arrays (host memory) or torch tensors (host or CUDA memory). ``check``
+turns a status into an exception carrying ``sdot_last_error()``. The library must
+be built (``paper_2110_08868_gb300.build``); there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsdot.so")
+
+SDOT_OK = 0
+ERRORS = {
+    -1: "SDOT_ERR_ARG", -2: "SDOT_ERR_MASS", -3: "SDOT_ERR_DUPLICATE", -4: "SDOT_ERR_TOO_FEW",
+    -5: "SDOT_ERR_OOM", -6: "SDOT_ERR_NO_DESCENT", -7: "SDOT_ERR_MAXIT",
+    -8: "SDOT_ERR_EMPTY_CELL", -9: "SDOT_ERR_TIMEOUT", -10: "SDOT_ERR_CUDA",
+    -11: "SDOT_ERR_CAPACITY",
+}
+for _v, _n in ERRORS.items():
+    globals()[_n] = _v
+SDOT_PREC_FP64 = 0
+SDOT_PREC_MIXED = 1
+
+
+class sdot_options(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("precision", ctypes.c_int),
+                ("seeds_per_leaf", ctypes.c_double), ("cg_rtol", ctypes.c_double),
+                ("cg_maxit", ctypes.c_int), ("newton_maxit", ctypes.c_int),
+                ("alpha_min", ctypes.c_double), ("verbose", ctypes.c_int)]
+
+
+class sdot_csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class sdot_stats(ctypes.Structure):
+    _fields_ = [("newton_iters", ctypes.c_int), ("laguerre_evals", ctypes.c_int),
+                ("cg_iters", ctypes.c_int64), ("max_rel_err", ctypes.c_double),
+                ("l2_err", ctypes.c_double), ("min_vol", ctypes.c_double),
+                ("last_alpha", ctypes.c_double), ("requeued", ctypes.c_int64),
+                ("reclipped_fp64", ctypes.c_int64), ("ms_knn", ctypes.c_double),
+                ("ms_clip", ctypes.c_double), ("ms_cg", ctypes.c_double),
+                ("ms_total", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+# every symbol include/sdot.h declares
+EXPORTS = ["sdot_default_options", "sdot_create", "sdot_set_stream", "sdot_laguerre",
+           "sdot_solve", "sdot_csr_copy", "sdot_get_psi", "sdot_displacement", "sdot_knn",
+           "sdot_size", "sdot_destroy", "sdot_last_error"]
+
+_lib = None
+
+
+class SdotError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def load(path=LIB_PATH):
+    """Load libsdot.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libsdot.so is not built ({path}); run paper_2110_08868_gb300.build")
+    lib = ctypes.CDLL(path)
+    P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    lib.sdot_default_options.argtypes = [ctypes.POINTER(sdot_options)]
+    lib.sdot_create.argtypes = [P, P, I64, P, ctypes.POINTER(sdot_options), ctypes.POINTER(P)]
+    lib.sdot_set_stream.argtypes = [P, P]
+    lib.sdot_laguerre.argtypes = [P, P, P, P, ctypes.POINTER(sdot_csr)]
+    lib.sdot_solve.argtypes = [P, D, P, ctypes.POINTER(sdot_stats)]
+    lib.sdot_csr_copy.argtypes = [ctypes.POINTER(sdot_csr), P, P, P]
+    lib.sdot_get_psi.argtypes = [P, P]
+    lib.sdot_displacement.argtypes = [P, P]
+    lib.sdot_knn.argtypes = [P, P]
+    lib.sdot_size.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I)]
+    lib.sdot_destroy.argtypes = [P]
+    lib.sdot_destroy.restype = None
+    lib.sdot_last_error.argtypes = []
+    lib.sdot_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("sdot_destroy", "sdot_last_error"):
+            getattr(lib, name).restype = I
+    _lib = lib
+    return lib
+
+
+def _ptr(x, dtype=np.float64):
+    """Raw address of a numpy array or torch tensor (contiguous, right dtype)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):  # torch tensor
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        want = {np.float64: "torch.float64", np.int32: "torch.int32",
+                np.int64: "torch.int64"}[dtype]
+        if str(x.dtype) != want:
+            raise TypeError(f"expected {want}, got {x.dtype}")
+        return ctypes.c_void_p(x.data_ptr())
+    if not isinstance(x, np.ndarray) or x.dtype != dtype or not x.flags.c_contiguous:
+        raise TypeError(f"expected a C-contiguous numpy array of {np.dtype(dtype)}")
+    return ctypes.c_void_p(x.ctypes.data)
+
+
+def sdot_last_error():
+    return load().sdot_last_error().decode()
+
+
+def check(rc):
+    if rc != SDOT_OK:
+        raise SdotError(rc, sdot_last_error())
+    return rc
+
+
+def sdot_default_options(**kw):
+    o = sdot_options()
+    load().sdot_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = {"fp64": SDOT_PREC_FP64, "mixed": SDOT_PREC_MIXED}[v]
+        setattr(o, k, v)
+    return o
+
+
+def sdot_create(pos, mass, box, opt=None):
+    """Returns (rc, ctx). pos: N x 3 float64; mass: N float64 or None; box: 3 floats."""
+    lib = load()
+    n = int(pos.shape[0])
+    b = np.ascontiguousarray(np.broadcast_to(np.asarray(box, dtype=np.float64), (3,)))
+    ctx = ctypes.c_void_p()
+    rc = lib.sdot_create(_ptr(pos), _ptr(mass), n, ctypes.c_void_p(b.ctypes.data),
+                         ctypes.byref(opt) if opt is not None else None, ctypes.byref(ctx))
+    return rc, ctx
+
+
+def sdot_set_stream(ctx, stream):
+    """stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None."""
+    h = getattr(stream, "cuda_stream", stream)
+    return load().sdot_set_stream(ctx, ctypes.c_void_p(h) if h else None)
+
+
+def sdot_laguerre(ctx, psi=None, volumes=None, centroids=None, hess=None):
+    """hess: an sdot_csr() to receive borrowed device pointers, or None."""
+    return load().sdot_laguerre(ctx, _ptr(psi), _ptr(volumes), _ptr(centroids),
+                                ctypes.byref(hess) if hess is not None else None)
+
+
+def sdot_solve(ctx, tol, psi0=None, stats=None):
+    return load().sdot_solve(ctx, float(tol), _ptr(psi0),
+                             ctypes.byref(stats) if stats is not None else None)
+
+
+def sdot_get_psi(ctx, psi):
+    return load().sdot_get_psi(ctx, _ptr(psi))
+
+
+def sdot_displacement(ctx, disp):
+    return load().sdot_displacement(ctx, _ptr(disp))
+
+
+def sdot_knn(ctx, nbr):
+    return load().sdot_knn(ctx, _ptr(nbr, np.int32))
+
+
+def sdot_size(ctx):
+    n = ctypes.c_int64()
+    k = ctypes.c_int()
+    rc = load().sdot_size(ctx, ctypes.byref(n), ctypes.byref(k))
+    return rc, n.value, k.value
+
+
+def sdot_destroy(ctx):
+    if ctx:
+        load().sdot_destroy(ctx)
+
+
+class Solver:
+    """Owning convenience wrapper over one context (raises on errors)."""
+
+    def __init__(self, pos, box, mass=None, **opts):
+        self.opt = sdot_default_options(**opts)
+        rc, self.ctx = sdot_create(pos, mass, box, self.opt)
+        check(rc)
+        _, self.N, self.k = sdot_size(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            sdot_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def laguerre(self, psi=None, with_hessian=False, allow_empty=False):
+        vol = np.empty(self.N)
+        cen = np.empty((self.N, 3))
+        h = sdot_csr() if with_hessian else None
+        rc = sdot_laguerre(self.ctx, psi, vol, cen, h)
+        if not (allow_empty and rc == SDOT_ERR_EMPTY_CELL):
+            check(rc)
+        out = dict(vol=vol, centroid=cen, rc=rc)
+        if with_hessian:
+            out["hess"] = csr_to_scipy(h)
+        return out
+
+    def solve(self, tol, psi0=None):
+        st = sdot_stats()
+        check(sdot_solve(self.ctx, tol, psi0, st))
+        return st.as_dict()
+
+    def psi(self):
+        out = np.empty(self.N)
+        check(sdot_get_psi(self.ctx, out))
+        return out
+
+    def displacement(self):
+        out = np.empty((self.N, 3))
+        check(sdot_displacement(self.ctx, out))
+        return out
+
+    def knn(self):
+        out = np.empty((self.N, self.k), dtype=np.int32)
+        check(sdot_knn(self.ctx, out))
+        return out
+
+
+def sdot_csr_copy(h, row_ptr, col, val):
+    return load().sdot_csr_copy(ctypes.byref(h), _ptr(row_ptr, np.int64), _ptr(col, np.int32),
+                                _ptr(val))
+
+
+def csr_to_scipy(h):
+    """Copy a borrowed device CSR (sdot_csr) to a scipy.sparse.csr_matrix."""
+    import scipy.sparse as sp
+
+    rp = np.empty(h.n + 1, dtype=np.int64)
+    col = np.empty(h.nnz, dtype=np.int32)
+    val = np.empty(h.nnz, dtype=np.float64)
+    check(sdot_csr_copy(h, rp, col, val))
+    return sp.csr_matrix((val, col, rp), shape=(h.n, h.n))

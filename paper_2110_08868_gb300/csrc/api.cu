@@ -1,0 +1,572 @@
+// C ABI of libsdot (include/sdot.h) and the host damped-Newton driver.
+//
+// Newton reading (the paper cites Kitagawa-Merigot-Thibert for convergence of a
+// Newton method on the concave C^2 dual K, Sec. "Monge-Ampere-Kantorovich
+// Reconstruction"; the damping rule is theirs): eps0 = 1/2 min(min_j V_j(psi0),
+// min_j nu_j); the step is psi + alpha delta with the first alpha in 1, 1/2, 1/4 ...
+// such that min_j V_j >= eps0 (no cell empties, the constraint stated beside the
+// maximisation of K) and ||nu - V||_2 <= (1 - alpha/2) ||nu - V(psi)||_2.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <chrono>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace sdot {
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+}  // namespace sdot
+
+using namespace sdot;
+
+struct sdot_ctx {
+    DeviceState d;
+    sdot_options opt;
+    cudaStream_t stream = 0;
+    std::vector<void*> allocs;
+    void* temp = nullptr;
+    size_t temp_bytes = 0;
+    double* stage = nullptr;  // N * 3 doubles for host <-> device staging
+    int64_t nnz_cap = 0;
+    int64_t nnz = 0;
+    int64_t nnz_cap_u = 0;
+    bool eval_valid = false;  // last evaluation is at d.psi
+    float ms_knn = 0;
+    EvalResult last{};
+};
+
+namespace {
+
+int dev_alloc(sdot_ctx* c, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error(std::string("device allocation of ") + std::to_string(bytes) +
+                  " bytes failed: " + cudaGetErrorString(e));
+        return SDOT_ERR_OOM;
+    }
+    c->allocs.push_back(*p);
+    return SDOT_OK;
+}
+
+template <typename T>
+int alloc_n(sdot_ctx* c, T** p, int64_t n) {
+    return dev_alloc(c, (void**)p, (size_t)n * sizeof(T));
+}
+
+void dev_free(sdot_ctx* c, void* p) {
+    if (!p) return;
+    for (size_t t = 0; t < c->allocs.size(); t++)
+        if (c->allocs[t] == p) {
+            c->allocs.erase(c->allocs.begin() + t);
+            break;
+        }
+    cudaFree(p);
+}
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// device view of a caller vector of n doubles (copies host data into dst)
+int input_vec(sdot_ctx* c, const double* src, int64_t n, double* dst, const double** view) {
+    if (is_device_ptr(src)) {
+        *view = src;
+        return SDOT_OK;
+    }
+    SDOT_CUDA_TRY(cudaMemcpyAsync(dst, src, (size_t)n * 8, cudaMemcpyHostToDevice, c->stream));
+    *view = dst;
+    return SDOT_OK;
+}
+
+int check_opt(const sdot_options& o) {
+    if (o.k < 1 || o.k > KMAX) return SDOT_ERR_ARG;
+    if (o.precision != SDOT_PREC_FP64 && o.precision != SDOT_PREC_MIXED) return SDOT_ERR_ARG;
+    if (!(o.seeds_per_leaf > 0.05 && o.seeds_per_leaf < 1000)) return SDOT_ERR_ARG;
+    if (!(o.cg_rtol > 0 && o.cg_rtol < 1)) return SDOT_ERR_ARG;
+    if (o.cg_maxit < 1 || o.newton_maxit < 0) return SDOT_ERR_ARG;
+    if (!(o.alpha_min > 0 && o.alpha_min <= 1)) return SDOT_ERR_ARG;
+    return SDOT_OK;
+}
+
+int eval_at(sdot_ctx* c, const double* psi_sorted, EvalResult* r) {
+    int rc = evaluate_cells(c->d, psi_sorted, c->opt.precision, r, c->stream);
+    if (rc) return rc;
+    return SDOT_OK;
+}
+
+// error code for the flags of an evaluation that must be valid
+int eval_status(const EvalResult& r, const char* where) {
+    if (r.flags & CS_TOO_LARGE) {
+        set_error(std::string(where) +
+                  ": a cell reaches half a box length from its seed (too few seeds for "
+                  "minimum-image distances, or psi too far from balance)");
+        return SDOT_ERR_TOO_FEW;
+    }
+    if (r.flags & CS_CAPACITY) {
+        set_error(std::string(where) + ": a cell exceeded the polytope capacity (" +
+                  std::to_string(MAXP) + " planes, " + std::to_string(MAXT) + " vertices, " +
+                  std::to_string(FCAP) + " facets)");
+        return SDOT_ERR_CAPACITY;
+    }
+    return SDOT_OK;
+}
+
+int ensure_csr_capacity(sdot_ctx* c, int64_t nnz) {
+    if (nnz <= c->nnz_cap) return SDOT_OK;
+    dev_free(c, c->d.col);
+    dev_free(c, c->d.val);
+    c->d.col = nullptr;
+    c->d.val = nullptr;
+    int64_t cap = nnz + nnz / 4 + 1024;
+    int rc = alloc_n(c, &c->d.col, cap);
+    if (rc) return rc;
+    rc = alloc_n(c, &c->d.val, cap);
+    if (rc) return rc;
+    c->nnz_cap = cap;
+    return SDOT_OK;
+}
+
+// assemble the sorted CSR: count (fixes nnz), grow the arrays if needed, fill
+int build_csr(sdot_ctx* c) {
+    int64_t nnz = 0;
+    int rc = csr_count(c->d, &nnz, c->stream);
+    if (rc) return rc;
+    if ((rc = ensure_csr_capacity(c, nnz))) return rc;
+    if ((rc = csr_fill(c->d, c->stream))) return rc;
+    c->nnz = nnz;
+    return SDOT_OK;
+}
+
+void log_iter(const sdot_ctx* c, int it, const EvalResult& r, double alpha, int cg_it,
+              double cg_res, int trials) {
+    if (!c->opt.verbose) return;
+    fprintf(stderr,
+            "{\"newton_it\": %d, \"max_rel_err\": %.6e, \"l2_err\": %.6e, \"min_vol\": %.6e, "
+            "\"alpha\": %g, \"cg_iters\": %d, \"cg_rel_res\": %.3e, \"trials\": %d, "
+            "\"requeued\": %lld, \"reclipped_fp64\": %lld, \"clip_ms\": %.3f}\n",
+            it, r.max_rel_err, r.l2_err, r.min_vol, alpha, cg_it, cg_res, trials,
+            (long long)r.requeued, (long long)r.reclipped, r.ms);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sdot_last_error(void) { return g_err.c_str(); }
+
+int sdot_default_options(sdot_options* o) {
+    if (!o) return SDOT_ERR_ARG;
+    o->k = 24;
+    o->precision = SDOT_PREC_MIXED;
+    o->seeds_per_leaf = 2.0;
+    o->cg_rtol = 1e-3;
+    o->cg_maxit = 5000;
+    o->newton_maxit = 100;
+    o->alpha_min = 1.0 / (1 << 30);
+    o->verbose = 0;
+    return SDOT_OK;
+}
+
+void sdot_destroy(sdot_ctx* c) {
+    if (!c) return;
+    for (void* p : c->allocs) cudaFree(p);
+    c->allocs.clear();
+    delete c;
+}
+
+int sdot_set_stream(sdot_ctx* c, void* stream) {
+    if (!c) return SDOT_ERR_ARG;
+    c->stream = (cudaStream_t)stream;
+    return SDOT_OK;
+}
+
+int sdot_size(const sdot_ctx* c, int64_t* N, int* k) {
+    if (!c) return SDOT_ERR_ARG;
+    if (N) *N = c->d.N;
+    if (k) *k = c->d.k;
+    return SDOT_OK;
+}
+
+int sdot_create(const double* pos, const double* mass, int64_t N, const double box[3],
+                const sdot_options* opt, sdot_ctx** out) {
+    g_err.clear();
+    if (!out) {
+        set_error("sdot_create: out is NULL");
+        return SDOT_ERR_ARG;
+    }
+    *out = nullptr;
+    if (!pos || !box || N < 2 || N > (int64_t)INT32_MAX - 1) {
+        set_error("sdot_create: need pos, box and 2 <= N < 2^31");
+        return SDOT_ERR_ARG;
+    }
+    for (int a = 0; a < 3; a++)
+        if (!(box[a] > 0) || !isfinite(box[a])) {
+            set_error("sdot_create: box lengths must be finite and positive");
+            return SDOT_ERR_ARG;
+        }
+    sdot_ctx* c = new sdot_ctx();
+    sdot_default_options(&c->opt);
+    if (opt) c->opt = *opt;
+    if (check_opt(c->opt)) {
+        delete c;
+        set_error("sdot_create: invalid options");
+        return SDOT_ERR_ARG;
+    }
+    if (c->opt.k > N - 1) {
+        delete c;
+        set_error("sdot_create: k must be < N");
+        return SDOT_ERR_TOO_FEW;
+    }
+    DeviceState& d = c->d;
+    memset(&d, 0, sizeof d);
+    d.N = N;
+    d.k = c->opt.k;
+    for (int a = 0; a < 3; a++) d.L[a] = box[a];
+    const double boxvol = box[0] * box[1] * box[2];
+    d.a = cbrt(boxvol / (double)N);
+    int rc = SDOT_OK;
+    auto fail = [&](int code) {
+        sdot_destroy(c);
+        return code;
+    };
+    // grid dimensions (to size the temp buffer)
+    double h = cbrt(c->opt.seeds_per_leaf * boxvol / (double)N);
+    int64_t ncell = 1;
+    int G[3];
+    for (int a = 0; a < 3; a++) {
+        double g = floor(box[a] / h);
+        if (g < 1) g = 1;
+        if (g > 1024) g = 1024;
+        G[a] = (int)g;
+        ncell *= G[a];
+    }
+    if ((rc = alloc_n(c, &d.pos, N)) || (rc = alloc_n(c, &d.posf, N)) ||
+        (rc = alloc_n(c, &d.perm, N)) || (rc = alloc_n(c, &d.iperm, N)) ||
+        (rc = alloc_n(c, &d.nu, N)) || (rc = alloc_n(c, &d.psi, N)) ||
+        (rc = alloc_n(c, &d.psi_trial, N)) || (rc = alloc_n(c, &d.knn, N * d.k)) ||
+        (rc = alloc_n(c, &d.knn_d2k, N)) || (rc = alloc_n(c, &d.vol, N)) ||
+        (rc = alloc_n(c, &d.m1, N * 3)) || (rc = alloc_n(c, &d.anchor, N * 3)) ||
+        (rc = alloc_n(c, &d.status, N)) || (rc = alloc_n(c, &d.fcnt, N)) ||
+        (rc = alloc_n(c, &d.fcol, N * FCAP)) || (rc = alloc_n(c, &d.fval, N * FCAP)) ||
+        (rc = alloc_n(c, &d.queue, N)) || (rc = alloc_n(c, &d.queue64, N)) ||
+        (rc = alloc_n(c, &d.counters, 16)) || (rc = alloc_n(c, &d.row_ptr, N + 1)) ||
+        (rc = alloc_n(c, &d.rowcnt, N + 1)) || (rc = alloc_n(c, &d.x, N)) ||
+        (rc = alloc_n(c, &d.r, N)) || (rc = alloc_n(c, &d.z, N)) || (rc = alloc_n(c, &d.p, N)) ||
+        (rc = alloc_n(c, &d.q, N)) || (rc = alloc_n(c, &d.dinv, N)) ||
+        (rc = alloc_n(c, &d.partials, 1 << 20)) || (rc = alloc_n(c, &d.scal, 64)) ||
+        (rc = alloc_n(c, &d.grid.cell_start, ncell + 1)) || (rc = alloc_n(c, &c->stage, N * 3)))
+        return fail(rc);
+    d.delta = d.x;
+    size_t tb = (size_t)(((N * 4 + 255) / 256) * 256) + 2 * (size_t)(((ncell * 4 + 255) / 256) * 256) +
+                256 + scan_temp_bytes(ncell + 1) + 4096;
+    if ((rc = dev_alloc(c, &c->temp, tb))) return fail(rc);
+    c->temp_bytes = tb;
+    // pyramid of psi bounds: level 0 = grid cells, each level 4x coarser, top <= 4^3
+    {
+        Pyramid& P = d.pyr;
+        int dim[3] = {G[0], G[1], G[2]};
+        int64_t off = 0;
+        P.nlev = 0;
+        while (true) {
+            for (int a = 0; a < 3; a++) P.dim[P.nlev][a] = dim[a];
+            P.off[P.nlev] = off;
+            off += (int64_t)dim[0] * dim[1] * dim[2];
+            P.nlev++;
+            if ((dim[0] <= 4 && dim[1] <= 4 && dim[2] <= 4) || P.nlev == MAXLEV) break;
+            for (int a = 0; a < 3; a++) dim[a] = (dim[a] + 3) / 4;
+        }
+        if ((rc = alloc_n(c, &P.psimax, off))) return fail(rc);
+    }
+    cudaStream_t s = c->stream;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    // positions: device view (caller buffer or staging copy)
+    const double* posd = nullptr;
+    if ((rc = input_vec(c, pos, N * 3, c->stage, &posd))) return fail(rc);
+    if ((rc = build_grid(d, posd, c->opt.seeds_per_leaf, c->temp, s))) return fail(rc);
+    // masses in sorted order
+    if (mass) {
+        const double* md = nullptr;
+        if ((rc = input_vec(c, mass, N, c->stage, &md))) return fail(rc);
+        if ((rc = gather_from_user(d, md, d.nu, 1, s))) return fail(rc);
+    } else {
+        std::vector<double> u((size_t)N, boxvol / (double)N);
+        if (cudaMemcpyAsync(d.nu, u.data(), (size_t)N * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            set_error("sdot_create: copying masses failed");
+            return fail(SDOT_ERR_CUDA);
+        }
+    }
+    {
+        double msum = 0, mmin = 0;
+        if ((rc = check_masses(d, &msum, &mmin, s))) return fail(rc);
+        if (!(mmin > 0) || !(fabs(msum - boxvol) <= 1e-10 * boxvol)) {
+            set_error("sdot_create: masses must be positive and sum to the box volume (sum " +
+                      std::to_string(msum) + ", box " + std::to_string(boxvol) + ")");
+            return fail(SDOT_ERR_MASS);
+        }
+    }
+    int kflags = 0;
+    if ((rc = build_knn(d, s, &kflags))) return fail(rc);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&c->ms_knn, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (kflags & 1) {
+        set_error("sdot_create: two seeds share a position");
+        return fail(SDOT_ERR_DUPLICATE);
+    }
+    if (kflags & 2) {
+        set_error("sdot_create: fewer than k other seeds");
+        return fail(SDOT_ERR_TOO_FEW);
+    }
+    if (cudaMemsetAsync(d.psi, 0, (size_t)N * 8, s) != cudaSuccess ||
+        cudaMemsetAsync(d.anchor, 0, (size_t)N * 12, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        set_error("sdot_create: initialisation failed");
+        return fail(SDOT_ERR_CUDA);
+    }
+    *out = c;
+    return SDOT_OK;
+}
+
+int sdot_laguerre(sdot_ctx* c, const double* psi, double* volumes, double* centroids,
+                  sdot_csr* hess) {
+    g_err.clear();
+    if (!c) return SDOT_ERR_ARG;
+    DeviceState& d = c->d;
+    cudaStream_t s = c->stream;
+    int rc;
+    if (psi) {
+        const double* pv = nullptr;
+        if ((rc = input_vec(c, psi, d.N, c->stage, &pv))) return rc;
+        if ((rc = gather_from_user(d, pv, d.psi, 1, s))) return rc;
+    }
+    EvalResult r;
+    if ((rc = eval_at(c, d.psi, &r))) return rc;
+    c->last = r;
+    c->eval_valid = true;
+    if ((rc = eval_status(r, "sdot_laguerre"))) return rc;
+    auto out_vec = [&](double* dst, int w, bool cen) -> int {
+        bool dev = is_device_ptr(dst);
+        double* tgt = dev ? dst : c->stage;
+        int q = cen ? centroids_user(d, tgt, 1, s) : scatter_to_user(d, d.vol, tgt, w, s);
+        if (q) return q;
+        if (!dev) {
+            SDOT_CUDA_TRY(cudaMemcpyAsync(dst, tgt, (size_t)d.N * w * 8, cudaMemcpyDeviceToHost, s));
+            SDOT_CUDA_TRY(cudaStreamSynchronize(s));
+        }
+        return SDOT_OK;
+    };
+    if (volumes && (rc = out_vec(volumes, 1, false))) return rc;
+    if (centroids && (rc = out_vec(centroids, 3, true))) return rc;
+    if (hess) {
+        if ((rc = build_csr(c))) return rc;
+        if (c->nnz > c->nnz_cap_u) {
+            dev_free(c, d.col_u);
+            dev_free(c, d.val_u);
+            d.col_u = nullptr;
+            d.val_u = nullptr;
+            if (!d.row_ptr_u && (rc = alloc_n(c, &d.row_ptr_u, d.N + 1))) return rc;
+            if ((rc = alloc_n(c, &d.col_u, c->nnz_cap)) || (rc = alloc_n(c, &d.val_u, c->nnz_cap)))
+                return rc;
+            c->nnz_cap_u = c->nnz_cap;
+        }
+        if ((rc = assemble_csr_user(d, c->nnz, s))) return rc;
+        SDOT_CUDA_TRY(cudaStreamSynchronize(s));
+        hess->n = d.N;
+        hess->nnz = c->nnz;
+        hess->row_ptr = d.row_ptr_u;
+        hess->col = d.col_u;
+        hess->val = d.val_u;
+    }
+    if (r.n_empty > 0) {
+        set_error("sdot_laguerre: " + std::to_string(r.n_empty) + " empty cell(s)");
+        return SDOT_ERR_EMPTY_CELL;
+    }
+    return SDOT_OK;
+}
+
+int sdot_solve(sdot_ctx* c, double tol, const double* psi0, sdot_stats* st) {
+    g_err.clear();
+    if (!c || !(tol > 0)) {
+        set_error("sdot_solve: need a context and tol > 0");
+        return SDOT_ERR_ARG;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    DeviceState& d = c->d;
+    cudaStream_t s = c->stream;
+    int rc;
+    sdot_stats S;
+    memset(&S, 0, sizeof S);
+    S.ms_knn = c->ms_knn;
+    if (psi0) {
+        const double* pv = nullptr;
+        if ((rc = input_vec(c, psi0, d.N, c->stage, &pv))) return rc;
+        if ((rc = gather_from_user(d, pv, d.psi, 1, s))) return rc;
+    } else {
+        SDOT_CUDA_TRY(cudaMemsetAsync(d.psi, 0, (size_t)d.N * 8, s));
+    }
+    if ((rc = subtract_mean(d, d.psi, s))) return rc;
+    EvalResult ev;
+    if ((rc = eval_at(c, d.psi, &ev))) return rc;
+    c->eval_valid = true;
+    S.laguerre_evals = 1;
+    S.ms_clip += ev.ms;
+    if ((rc = eval_status(ev, "sdot_solve"))) return rc;
+    if (ev.n_empty > 0) {
+        set_error("sdot_solve: the initial psi has empty cells");
+        return SDOT_ERR_EMPTY_CELL;
+    }
+    double numin = 0, nusum = 0;
+    if ((rc = check_masses(d, &nusum, &numin, s))) return rc;
+    const double eps0 = 0.5 * fmin(ev.min_vol, numin);
+    cudaEvent_t c0, c1;
+    cudaEventCreate(&c0);
+    cudaEventCreate(&c1);
+    int it = 0;
+    double alpha = 1.0;
+    rc = SDOT_OK;
+    log_iter(c, it, ev, 0.0, 0, 0.0, 0);
+    while (ev.max_rel_err > tol) {
+        if (it >= c->opt.newton_maxit) {
+            set_error("sdot_solve: Newton reached newton_maxit");
+            rc = SDOT_ERR_MAXIT;
+            break;
+        }
+        if ((rc = build_csr(c))) break;
+        int cg_it = 0;
+        double cg_res = 0;
+        cudaEventRecord(c0, s);
+        if ((rc = pcg_solve(d, c->opt.cg_rtol, c->opt.cg_maxit, &cg_it, &cg_res, s))) break;
+        cudaEventRecord(c1, s);
+        cudaEventSynchronize(c1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, c0, c1);
+        S.ms_cg += ms;
+        S.cg_iters += cg_it;
+        alpha = 1.0;
+        int trials = 0;
+        EvalResult et;
+        while (true) {
+            if ((rc = axpy_gauge(d, d.psi, d.x, alpha, d.psi_trial, s))) break;
+            if ((rc = eval_at(c, d.psi_trial, &et))) break;
+            trials++;
+            S.laguerre_evals++;
+            S.ms_clip += et.ms;
+            bool valid = !(et.flags & (CS_TOO_LARGE | CS_CAPACITY));
+            if (valid && et.min_vol >= eps0 && et.l2_err <= (1.0 - 0.5 * alpha) * ev.l2_err) break;
+            alpha *= 0.5;
+            if (alpha < c->opt.alpha_min) {
+                set_error("sdot_solve: line search step below alpha_min");
+                rc = SDOT_ERR_NO_DESCENT;
+                break;
+            }
+        }
+        if (rc) break;
+        double* t = d.psi;
+        d.psi = d.psi_trial;
+        d.psi_trial = t;
+        if ((rc = subtract_mean(d, d.psi, s))) break;
+        ev = et;
+        it++;
+        log_iter(c, it, ev, alpha, cg_it, cg_res, trials);
+    }
+    cudaEventDestroy(c0);
+    cudaEventDestroy(c1);
+    c->last = ev;
+    c->eval_valid = true;
+    S.newton_iters = it;
+    S.max_rel_err = ev.max_rel_err;
+    S.l2_err = ev.l2_err;
+    S.min_vol = ev.min_vol;
+    S.last_alpha = alpha;
+    S.requeued = ev.requeued;
+    S.reclipped_fp64 = ev.reclipped;
+    cudaStreamSynchronize(s);
+    S.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (st) *st = S;
+    return rc;
+}
+
+int sdot_csr_copy(const sdot_csr* h, int64_t* row_ptr, int32_t* col, double* val) {
+    g_err.clear();
+    if (!h || !row_ptr || !col || !val) {
+        set_error("sdot_csr_copy: NULL argument");
+        return SDOT_ERR_ARG;
+    }
+    SDOT_CUDA_TRY(cudaMemcpy(row_ptr, h->row_ptr, (size_t)(h->n + 1) * 8, cudaMemcpyDefault));
+    SDOT_CUDA_TRY(cudaMemcpy(col, h->col, (size_t)h->nnz * 4, cudaMemcpyDefault));
+    SDOT_CUDA_TRY(cudaMemcpy(val, h->val, (size_t)h->nnz * 8, cudaMemcpyDefault));
+    return SDOT_OK;
+}
+
+int sdot_get_psi(sdot_ctx* c, double* psi) {
+    g_err.clear();
+    if (!c || !psi) return SDOT_ERR_ARG;
+    DeviceState& d = c->d;
+    bool dev = is_device_ptr(psi);
+    double* tgt = dev ? psi : c->stage;
+    int rc = scatter_to_user(d, d.psi, tgt, 1, c->stream);
+    if (rc) return rc;
+    if (!dev) SDOT_CUDA_TRY(cudaMemcpyAsync(psi, tgt, (size_t)d.N * 8, cudaMemcpyDeviceToHost, c->stream));
+    SDOT_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return SDOT_OK;
+}
+
+int sdot_displacement(sdot_ctx* c, double* disp) {
+    g_err.clear();
+    if (!c || !disp) return SDOT_ERR_ARG;
+    DeviceState& d = c->d;
+    int rc;
+    if (!c->eval_valid) {
+        EvalResult r;
+        if ((rc = eval_at(c, d.psi, &r))) return rc;
+        c->last = r;
+        c->eval_valid = true;
+        if ((rc = eval_status(r, "sdot_displacement"))) return rc;
+    }
+    bool dev = is_device_ptr(disp);
+    double* tgt = dev ? disp : c->stage;
+    if ((rc = centroids_user(d, tgt, 0, c->stream))) return rc;
+    if (!dev)
+        SDOT_CUDA_TRY(cudaMemcpyAsync(disp, tgt, (size_t)d.N * 24, cudaMemcpyDeviceToHost, c->stream));
+    SDOT_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return SDOT_OK;
+}
+
+int sdot_knn(sdot_ctx* c, int32_t* nbr) {
+    g_err.clear();
+    if (!c || !nbr) return SDOT_ERR_ARG;
+    DeviceState& d = c->d;
+    bool dev = is_device_ptr(nbr);
+    int32_t* tgt = nbr;
+    int rc;
+    if (!dev && (rc = alloc_n(c, &tgt, d.N * d.k))) return rc;
+    rc = knn_to_user(d, tgt, c->stream);
+    if (!rc && !dev &&
+        cudaMemcpyAsync(nbr, tgt, (size_t)d.N * d.k * 4, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        rc = SDOT_ERR_CUDA;
+    if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = SDOT_ERR_CUDA;
+    if (!dev) dev_free(c, tgt);
+    if (rc == SDOT_ERR_CUDA) set_error("sdot_knn: copy failed");
+    return rc;
+}
+
+}  // extern "C"

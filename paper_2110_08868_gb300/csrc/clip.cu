@@ -1,0 +1,1067 @@
+// Laguerre cell clipping: volumes, first moments and facet areas of every cell.
+//
+// Cell i of eq. (laguerrecell) in seed-local coordinates p = q - y_i is
+//     P_i = { p : p.d_ij <= b_ij for all j },  d_ij = minimum image of y_j - y_i,
+//     b_ij = 1/2 |d_ij|^2 + psi_i - psi_j,
+// the lifted power bisectors of the neighbours. Coordinates are scaled by the
+// length unit a = (|box|/N)^(1/3) and psi by a^2 so every quantity is O(1).
+//
+// One warp owns one cell. The polytope lives in shared memory as planes plus its
+// vertices, each vertex a "dual triangle" of the three planes through it, oriented
+// so that det(n_a, n_b, n_c) > 0. Clipping by a new plane: the lanes classify the
+// vertices (one ballot), the removed vertices' dual edges whose reverse edge is
+// not removed form the boundary cycle, and every boundary edge (a -> b) yields the
+// new vertex (a, b, new plane). Integration walks each face's vertex cycle and
+// sums fan tetrahedra from the seed (volume, first moment, area vector).
+//
+// Neighbour search: the k nearest seeds first, then a security test. The test
+// walks a pyramid of per-node upper bounds of psi and proves, node by node, that no
+// other seed's plane can reach the polytope:
+//     seed j cannot cut if  z.d + R_z |d| <= b_ij
+// for any anchor z with R_z = max_vertex |v - z| (z: the cell's previous local
+// centroid). For a node B with distance u from the anchor, distance at most dmax
+// from the seed and psi bound psimax_B this holds for every seed inside when
+//     1/2 u^2 - 1/2 |z|^2 - R_z dmax - (psimax_B - psi_i) >= 0.
+// A cell whose test finds a seed that actually cuts it is re-queued; the re-queue
+// pass clips every such seed during the same walk. In mixed precision the geometry
+// runs in FP32 (planes built in FP64, sums accumulated in FP64) and cells failing
+// the consistency check (non-closed surface, broken face cycle, badly conditioned
+// vertex, capacity) are re-clipped in FP64.
+#include <float.h>
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace sdot {
+
+#define FULLMASK 0xffffffffu
+
+template <typename R>
+struct V3 {
+    R x, y, z;
+};
+template <typename R>
+struct V4 {
+    R x, y, z, w;
+};
+
+template <typename R>
+struct WarpPoly {
+    V4<R> pl[MAXP];         // plane p.n <= w, n = d/a, w = b/a^2
+    R plen[MAXP];           // |n|
+    int32_t pj[MAXP];       // neighbour (sorted index) or -1 for a box face
+    uint32_t tri[MAXT];     // plane slots a | b << 8 | c << 16
+    V3<R> v[MAXT];          // vertex positions
+    uint32_t scratch[MAXT]; // removed vertices during a clip
+    uint32_t fresh[MAXT];   // new vertices during a clip
+    uint32_t stack[STACK];  // traversal stack: level << 27 | node
+    int np, nt;
+};
+
+struct ClipParams {
+    int64_t N;
+    int k;
+    double a, inv_a, inv_a2;
+    double L[3], halfL[3];
+    float Lt[3], halfLt[3];  // box in units of a
+    float ht[3];             // grid cell size in units of a
+    int G[3];
+    const Pos4* pos;
+    const float4* posf;
+    const double* psi;
+    const int32_t* knn;
+    const double* knn_d2k;
+    const int32_t* cell_start;
+    Pyramid pyr;
+    // outputs
+    double* vol;
+    double* m1;
+    float* anchor;
+    uint8_t* status;
+    int32_t* fcnt;
+    int32_t* fcol;
+    double* fval;
+    int32_t* queue_out;
+    int32_t* queue_cnt;
+    int32_t* q64_out;
+    int32_t* q64_cnt;
+    int32_t* work_counter;
+    const int32_t* worklist;  // null: cells 0..nwork-1
+    int64_t nwork;
+};
+
+__device__ __forceinline__ double wrapd(double dx, double L, double halfL) {
+    if (dx > halfL) return dx - L;
+    if (dx < -halfL) return dx + L;
+    return dx;
+}
+__device__ __forceinline__ float wrapf(float dx, float L, float halfL) {
+    if (dx > halfL) return dx - L;
+    if (dx < -halfL) return dx + L;
+    return dx;
+}
+__device__ __forceinline__ double exact_d2(const Pos4& a, const Pos4& b,
+                                           const ClipParams& p) {
+    double dx = wrapd(__dsub_rn(b.x, a.x), p.L[0], p.halfL[0]);
+    double dy = wrapd(__dsub_rn(b.y, a.y), p.L[1], p.halfL[1]);
+    double dz = wrapd(__dsub_rn(b.z, a.z), p.L[2], p.halfL[2]);
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+__device__ __forceinline__ uint32_t pack3(uint32_t a, uint32_t b, uint32_t c) {
+    return a | (b << 8) | (c << 16);
+}
+__device__ __forceinline__ bool has_edge(uint32_t t, uint32_t x, uint32_t y) {
+    // does triangle t contain the directed edge x -> y
+    uint32_t a = t & 0xff, b = (t >> 8) & 0xff, c = (t >> 16) & 0xff;
+    return (a == x && b == y) || (b == x && c == y) || (c == x && a == y);
+}
+
+template <typename R>
+__device__ __forceinline__ R warp_max(R v) {
+    for (int o = 16; o > 0; o >>= 1) {
+        R u = __shfl_xor_sync(FULLMASK, v, o);
+        v = v > u ? v : u;
+    }
+    return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULLMASK, v, o);
+    return v;
+}
+
+// the box [-L/2, L/2]^3: bisectors with the seed's own six face images
+template <typename R>
+__device__ void poly_init(WarpPoly<R>& P, const ClipParams& cp, int lane) {
+    if (lane < 6) {
+        int ax = lane >> 1;
+        R s = (lane & 1) ? R(-1) : R(1);
+        R Lt = (R)cp.Lt[ax];
+        V4<R> pl;
+        pl.x = ax == 0 ? s * Lt : R(0);
+        pl.y = ax == 1 ? s * Lt : R(0);
+        pl.z = ax == 2 ? s * Lt : R(0);
+        pl.w = R(0.5) * Lt * Lt;
+        P.pl[lane] = pl;
+        P.plen[lane] = Lt;
+        P.pj[lane] = -1;
+    }
+    if (lane < 8) {
+        int sx = (lane & 1) ? 1 : -1, sy = (lane & 2) ? 1 : -1, sz = (lane & 4) ? 1 : -1;
+        uint32_t X = sx > 0 ? 0 : 1, Y = sy > 0 ? 2 : 3, Z = sz > 0 ? 4 : 5;
+        P.tri[lane] = (sx * sy * sz > 0) ? pack3(X, Y, Z) : pack3(X, Z, Y);
+        V3<R> v;
+        v.x = R(0.5) * (R)cp.Lt[0] * (R)sx;
+        v.y = R(0.5) * (R)cp.Lt[1] * (R)sy;
+        v.z = R(0.5) * (R)cp.Lt[2] * (R)sz;
+        P.v[lane] = v;
+    }
+    if (lane == 0) {
+        P.np = 6;
+        P.nt = 8;
+    }
+    __syncwarp();
+}
+
+template <typename R>
+__device__ __forceinline__ V3<R> vertex_of(const WarpPoly<R>& P, uint32_t t, R& det_rel) {
+    const V4<R> A = P.pl[t & 0xff], B = P.pl[(t >> 8) & 0xff], C = P.pl[(t >> 16) & 0xff];
+    // n_b x n_c, n_c x n_a, n_a x n_b
+    R bcx = B.y * C.z - B.z * C.y, bcy = B.z * C.x - B.x * C.z, bcz = B.x * C.y - B.y * C.x;
+    R cax = C.y * A.z - C.z * A.y, cay = C.z * A.x - C.x * A.z, caz = C.x * A.y - C.y * A.x;
+    R abx = A.y * B.z - A.z * B.y, aby = A.z * B.x - A.x * B.z, abz = A.x * B.y - A.y * B.x;
+    R det = A.x * bcx + A.y * bcy + A.z * bcz;
+    R inv = R(1) / det;
+    V3<R> v;
+    v.x = (A.w * bcx + B.w * cax + C.w * abx) * inv;
+    v.y = (A.w * bcy + B.w * cay + C.w * aby) * inv;
+    v.z = (A.w * bcz + B.w * caz + C.w * abz) * inv;
+    R la = P.plen[t & 0xff], lb = P.plen[(t >> 8) & 0xff], lc = P.plen[(t >> 16) & 0xff];
+    det_rel = det / (la * lb * lc);
+    return v;
+}
+
+// drop planes no vertex references any more; returns the number of planes left
+template <typename R>
+__device__ int poly_gc(WarpPoly<R>& P, int lane) {
+    uint32_t lo = 0, hi = 0;
+    for (int s = lane; s < P.nt; s += 32) {
+        uint32_t t = P.tri[s];
+        for (int e = 0; e < 3; e++) {
+            uint32_t q = (t >> (8 * e)) & 0xff;
+            if (q < 32) lo |= 1u << q;
+            else hi |= 1u << (q - 32);
+        }
+    }
+    lo = __reduce_or_sync(FULLMASK, lo);
+    hi = __reduce_or_sync(FULLMASK, hi);
+    lo |= 0x3fu;  // box planes keep their slots
+    int np = P.np;
+    // remap table: new slot of plane q = number of used planes below q
+    V4<R> pl0, pl1;
+    R len0 = 0, len1 = 0;
+    int32_t j0 = 0, j1 = 0;
+    bool u0 = lane < np && (lo >> lane & 1), u1 = lane + 32 < np && (hi >> lane & 1);
+    if (u0) { pl0 = P.pl[lane]; len0 = P.plen[lane]; j0 = P.pj[lane]; }
+    if (u1) { pl1 = P.pl[lane + 32]; len1 = P.plen[lane + 32]; j1 = P.pj[lane + 32]; }
+    uint32_t below = (lane == 0) ? 0u : ((1u << lane) - 1u);
+    int n0 = __popc(lo & below);
+    int n1 = __popc(lo) + __popc(hi & below);
+    __syncwarp();
+    if (u0) { P.pl[n0] = pl0; P.plen[n0] = len0; P.pj[n0] = j0; }
+    if (u1) { P.pl[n1] = pl1; P.plen[n1] = len1; P.pj[n1] = j1; }
+    __syncwarp();
+    for (int s = lane; s < P.nt; s += 32) {
+        uint32_t t = P.tri[s], r = 0;
+        for (int e = 0; e < 3; e++) {
+            uint32_t q = (t >> (8 * e)) & 0xff;
+            uint32_t nq = q < 32 ? __popc(lo & ((q == 0) ? 0u : ((1u << q) - 1u)))
+                                 : __popc(lo) + __popc(hi & (((q - 32) == 0) ? 0u : ((1u << (q - 32)) - 1u)));
+            r |= nq << (8 * e);
+        }
+        P.tri[s] = r;
+    }
+    int nn = __popc(lo) + __popc(hi);
+    __syncwarp();
+    if (lane == 0) P.np = nn;
+    __syncwarp();
+    return nn;
+}
+
+enum { CLIP_NONE = 0, CLIP_CUT = 1, CLIP_EMPTY = 2, CLIP_CAP = 3 };
+
+// Clip by p.n <= w (tag j). FP32 conditioning problems set *bad.
+template <typename R>
+__device__ int poly_clip(WarpPoly<R>& P, const V4<R>& pn, R plen, int32_t j, int lane,
+                         bool& bad) {
+    const int nt = P.nt;
+    bool out[MAXT / 32];
+    uint32_t m[MAXT / 32];
+    int nrem = 0;
+#pragma unroll
+    for (int t = 0; t < MAXT / 32; t++) {
+        int s = lane + 32 * t;
+        out[t] = false;
+        if (s < nt) {
+            V3<R> v = P.v[s];
+            out[t] = v.x * pn.x + v.y * pn.y + v.z * pn.z - pn.w > R(0);
+        }
+        m[t] = __ballot_sync(FULLMASK, out[t]);
+        nrem += __popc(m[t]);
+    }
+    if (nrem == 0) return CLIP_NONE;
+    if (nrem == nt) return CLIP_EMPTY;
+    if (P.np >= MAXP) {
+        if (poly_gc(P, lane) >= MAXP) return CLIP_CAP;
+    }
+    const uint32_t ps = (uint32_t)P.np;
+    const uint32_t below = (lane == 0) ? 0u : ((1u << lane) - 1u);
+    // removed list
+    {
+        int base = 0;
+#pragma unroll
+        for (int t = 0; t < MAXT / 32; t++) {
+            if (out[t]) P.scratch[base + __popc(m[t] & below)] = P.tri[lane + 32 * t];
+            base += __popc(m[t]);
+        }
+    }
+    __syncwarp();
+    // boundary edges of the removed region
+    uint32_t bmask = 0;  // 3 bits per removed entry handled by this lane
+    int cnt = 0;
+    for (int r = lane, e = 0; r < nrem; r += 32, e++) {
+        uint32_t t = P.scratch[r];
+        uint32_t a = t & 0xff, b = (t >> 8) & 0xff, c = (t >> 16) & 0xff;
+        bool fab = false, fbc = false, fca = false;
+        for (int q = 0; q < nrem; q++) {
+            uint32_t u = P.scratch[q];
+            fab |= has_edge(u, b, a);
+            fbc |= has_edge(u, c, b);
+            fca |= has_edge(u, a, c);
+        }
+        uint32_t bits = (fab ? 0u : 1u) | (fbc ? 0u : 2u) | (fca ? 0u : 4u);
+        bmask |= bits << (3 * e);
+        cnt += __popc(bits);
+    }
+    // warp exclusive scan of cnt
+    int incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(FULLMASK, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int nnew = __shfl_sync(FULLMASK, incl, 31);
+    const int nkept = nt - nrem;
+    if (nkept + nnew > MAXT) return CLIP_CAP;
+    {
+        int pos = incl - cnt;
+        for (int r = lane, e = 0; r < nrem; r += 32, e++) {
+            uint32_t t = P.scratch[r];
+            uint32_t a = t & 0xff, b = (t >> 8) & 0xff, c = (t >> 16) & 0xff;
+            uint32_t bits = (bmask >> (3 * e)) & 7u;
+            if (bits & 1u) P.fresh[pos++] = pack3(a, b, ps);
+            if (bits & 2u) P.fresh[pos++] = pack3(b, c, ps);
+            if (bits & 4u) P.fresh[pos++] = pack3(c, a, ps);
+        }
+    }
+    // compact the kept vertices
+    {
+        uint32_t kt[MAXT / 32];
+        V3<R> kv[MAXT / 32];
+        int dst[MAXT / 32];
+        int base = 0;
+#pragma unroll
+        for (int t = 0; t < MAXT / 32; t++) {
+            int s = lane + 32 * t;
+            uint32_t km = __ballot_sync(FULLMASK, s < nt && !out[t]);
+            dst[t] = -1;
+            if (s < nt && !out[t]) {
+                kt[t] = P.tri[s];
+                kv[t] = P.v[s];
+                dst[t] = base + __popc(km & below);
+            }
+            base += __popc(km);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < MAXT / 32; t++)
+            if (dst[t] >= 0) {
+                P.tri[dst[t]] = kt[t];
+                P.v[dst[t]] = kv[t];
+            }
+    }
+    if (lane == 0) {
+        P.pl[ps] = pn;
+        P.plen[ps] = plen;
+        P.pj[ps] = j;
+        P.np = ps + 1;
+        P.nt = nkept + nnew;
+    }
+    __syncwarp();
+    bool lbad = false;
+    for (int n = lane; n < nnew; n += 32) {
+        uint32_t t = P.fresh[n];
+        R det_rel;
+        V3<R> v = vertex_of(P, t, det_rel);
+        if (!(det_rel > R(sizeof(R) == 4 ? 1e-6 : 1e-14))) lbad = true;
+        P.tri[nkept + n] = t;
+        P.v[nkept + n] = v;
+    }
+    if (__any_sync(FULLMASK, lbad)) bad = true;
+    __syncwarp();
+    return CLIP_CUT;
+}
+
+template <typename R>
+__device__ R poly_radius(const WarpPoly<R>& P, V3<R> z, int lane) {
+    R r2 = 0;
+    for (int s = lane; s < P.nt; s += 32) {
+        V3<R> v = P.v[s];
+        R dx = v.x - z.x, dy = v.y - z.y, dz = v.z - z.z;
+        R q = dx * dx + dy * dy + dz * dz;
+        r2 = q > r2 ? q : r2;
+    }
+    r2 = warp_max(r2);
+    return sqrt(r2);
+}
+
+// plane of neighbour j for cell i, built in FP64 (normalised units)
+__device__ __forceinline__ void make_plane(const ClipParams& cp, const Pos4& yi, double psii,
+                                           int32_t j, double& nx, double& ny, double& nz,
+                                           double& w) {
+    Pos4 yj = cp.pos[j];
+    nx = wrapd(yj.x - yi.x, cp.L[0], cp.halfL[0]) * cp.inv_a;
+    ny = wrapd(yj.y - yi.y, cp.L[1], cp.halfL[1]) * cp.inv_a;
+    nz = wrapd(yj.z - yi.z, cp.L[2], cp.halfL[2]) * cp.inv_a;
+    w = 0.5 * (nx * nx + ny * ny + nz * nz) + (psii - cp.psi[j]) * cp.inv_a2;
+}
+
+__device__ __forceinline__ float circ_gap(float p, float lo, float hi, float Lt) {
+    // distance from p to the interval [lo, hi] on a circle of length Lt
+    if (p >= lo && p <= hi) return 0.f;
+    float d1 = lo - p;
+    if (d1 < 0.f) d1 += Lt;
+    float d2 = p - hi;
+    if (d2 < 0.f) d2 += Lt;
+    return fminf(d1, d2);
+}
+__device__ __forceinline__ float circ_far(float p, float lo, float hi, float Lt) {
+    // largest circular distance from p to a point of [lo, hi]
+    float A = p + 0.5f * Lt;
+    if (A >= Lt) A -= Lt;
+    if (A >= lo && A <= hi) return 0.5f * Lt;
+    float e1 = fabsf(lo - p), e2 = fabsf(hi - p);
+    e1 = fminf(e1, Lt - e1);
+    e2 = fminf(e2, Lt - e2);
+    return fmaxf(e1, e2);
+}
+
+struct Anchor {
+    float z[3];      // anchor, local (units of a)
+    float zabs[3];   // anchor, absolute (units of a), wrapped
+    float yabs[3];   // seed, absolute (units of a)
+    float z2h;       // 1/2 |z|^2
+    float psi_i;     // psi_i / a^2
+};
+
+// true when every seed of node (level l, coordinates X, Y, Z) provably cannot cut
+__device__ __forceinline__ bool node_pruned(const ClipParams& cp, const Anchor& an, float Rz,
+                                            int l, int X, int Y, int Z) {
+    float pm = cp.pyr.psimax[cp.pyr.off[l] +
+                             ((int64_t)Z * cp.pyr.dim[l][1] + Y) * cp.pyr.dim[l][0] + X];
+    if (pm == -INFINITY) return true;  // no seed inside
+    int span = 1 << (2 * l);
+    int c[3] = {X, Y, Z};
+    float u2 = 0.f, dm2 = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        int c0 = c[a] * span, c1 = min((c[a] + 1) * span, cp.G[a]);
+        float lo = c0 * cp.ht[a], hi = (c1 == cp.G[a]) ? cp.Lt[a] : c1 * cp.ht[a];
+        float g = circ_gap(an.zabs[a], lo, hi, cp.Lt[a]);
+        float f = circ_far(an.yabs[a], lo, hi, cp.Lt[a]);
+        u2 += g * g;
+        dm2 += f * f;
+    }
+    float dmax = sqrtf(dm2);
+    float t1 = 0.5f * u2, t2 = Rz * dmax, dpsi = pm - an.psi_i;
+    float val = t1 - an.z2h - t2 - dpsi;
+    float margin = 1e-5f * (t1 + an.z2h + t2 + fabsf(pm) + fabsf(an.psi_i)) + 1e-6f;
+    return val > margin;
+}
+
+// conservative FP32 test: can seed j's plane reach the polytope (anchor z, radius Rz)
+__device__ __forceinline__ bool seed_may_cut(const ClipParams& cp, const Anchor& an, float Rz,
+                                             const float4& yj) {
+    float dx = wrapf(yj.x - an.yabs[0], cp.Lt[0], cp.halfLt[0]);
+    float dy = wrapf(yj.y - an.yabs[1], cp.Lt[1], cp.halfLt[1]);
+    float dz = wrapf(yj.z - an.yabs[2], cp.Lt[2], cp.halfLt[2]);
+    float d2 = dx * dx + dy * dy + dz * dz;
+    float dl = sqrtf(d2);
+    float b = 0.5f * d2 + an.psi_i - yj.w;
+    float lhs = an.z[0] * dx + an.z[1] * dy + an.z[2] * dz + Rz * dl;
+    float margin = 1e-5f * (fabsf(lhs) + 0.5f * d2 + fabsf(an.psi_i) + fabsf(yj.w)) + 1e-6f;
+    return lhs > b - margin;
+}
+
+enum { MODE_CERTIFY = 0, MODE_FULL = 1 };
+
+// Walk the pyramid. MODE_CERTIFY: return false as soon as an unseen seed cuts the
+// polytope. MODE_FULL: clip every such seed. Returns true when the walk completed.
+template <typename R, int MODE>
+__device__ bool traverse(WarpPoly<R>& P, const ClipParams& cp, int64_t i, const Pos4& yi,
+                         double psii, const Anchor& an, double d2k, int ok_k, int lane,
+                         bool& bad, uint32_t& st) {
+    V3<R> zr;
+    zr.x = (R)an.z[0];
+    zr.y = (R)an.z[1];
+    zr.z = (R)an.z[2];
+    float Rz = (float)poly_radius(P, zr, lane) * 1.0001f + 1e-6f;
+    const int top = cp.pyr.nlev;  // virtual root level
+    int sp = 0;
+    if (lane == 0) P.stack[0] = (uint32_t)top << 27;
+    sp = 1;
+    __syncwarp();
+    while (sp > 0) {
+        uint32_t e = P.stack[sp - 1];
+        sp--;
+        __syncwarp();
+        int l = (int)(e >> 27);
+        int node = (int)(e & ((1u << 27) - 1));
+        int cl = l - 1;
+        int cdx = cp.pyr.dim[cl][0], cdy = cp.pyr.dim[cl][1], cdz = cp.pyr.dim[cl][2];
+        int x0, y0, z0, nx, ny, nz;
+        if (l == top) {
+            x0 = y0 = z0 = 0;
+            nx = cdx;
+            ny = cdy;
+            nz = cdz;
+        } else {
+            int pdx = cp.pyr.dim[l][0], pdy = cp.pyr.dim[l][1];
+            int X = node % pdx, Y = (node / pdx) % pdy, Z = node / (pdx * pdy);
+            x0 = 4 * X;
+            y0 = 4 * Y;
+            z0 = 4 * Z;
+            nx = min(4, cdx - x0);
+            ny = min(4, cdy - y0);
+            nz = min(4, cdz - z0);
+        }
+        const int nch = nx * ny * nz;  // <= 64
+        for (int base = 0; base < nch; base += 32) {
+            int t = base + lane;
+            bool surv = false;
+            int cx = 0, cy = 0, cz = 0;
+            if (t < nch) {
+                cx = x0 + t % nx;
+                cy = y0 + (t / nx) % ny;
+                cz = z0 + t / (nx * ny);
+                surv = !node_pruned(cp, an, Rz, cl, cx, cy, cz);
+            }
+            uint32_t sm = __ballot_sync(FULLMASK, surv);
+            if (sm == 0) continue;
+            if (cl > 0) {
+                int n = __popc(sm);
+                if (sp + n > STACK) {
+                    st |= CS_CAPACITY;
+                    return false;
+                }
+                uint32_t below = (lane == 0) ? 0u : ((1u << lane) - 1u);
+                if (surv)
+                    P.stack[sp + __popc(sm & below)] =
+                        ((uint32_t)cl << 27) |
+                        (uint32_t)(((int64_t)cz * cdy + cy) * cdx + cx);
+                sp += n;
+                __syncwarp();
+                continue;
+            }
+            // surviving leaves: test their seeds
+            while (sm) {
+                int src = __ffs(sm) - 1;
+                sm &= sm - 1;
+                int lx = __shfl_sync(FULLMASK, cx, src);
+                int ly = __shfl_sync(FULLMASK, cy, src);
+                int lz = __shfl_sync(FULLMASK, cz, src);
+                int64_t leaf = ((int64_t)lz * cp.G[1] + ly) * cp.G[0] + lx;
+                int32_t sb = cp.cell_start[leaf], se = cp.cell_start[leaf + 1];
+                for (int32_t s0 = sb; s0 < se; s0 += 32) {
+                    int32_t s = s0 + lane;
+                    bool cand = false;
+                    if (s < se && s != (int32_t)i) cand = seed_may_cut(cp, an, Rz, cp.posf[s]);
+                    uint32_t cm = __ballot_sync(FULLMASK, cand);
+                    while (cm) {
+                        int cl2 = __ffs(cm) - 1;
+                        cm &= cm - 1;
+                        int32_t j = s0 + cl2;
+                        // seen in the kNN list?
+                        Pos4 yj = cp.pos[j];
+                        double d2 = exact_d2(yi, yj, cp);
+                        int oj = (int)yj.w;
+                        if (d2 < d2k || (d2 == d2k && oj <= ok_k)) continue;
+                        // already a plane of the polytope?
+                        bool dup = (lane < P.np && P.pj[lane] == j) ||
+                                   (lane + 32 < P.np && P.pj[lane + 32] == j);
+                        if (__any_sync(FULLMASK, dup)) continue;
+                        double nxd, nyd, nzd, wd;
+                        make_plane(cp, yi, psii, j, nxd, nyd, nzd, wd);
+                        V4<R> pn;
+                        pn.x = (R)nxd;
+                        pn.y = (R)nyd;
+                        pn.z = (R)nzd;
+                        pn.w = (R)wd;
+                        R plen = (R)sqrt(nxd * nxd + nyd * nyd + nzd * nzd);
+                        if (MODE == MODE_CERTIFY) {
+                            // does it actually cut? (classification only)
+                            bool o = false;
+                            for (int q = lane; q < P.nt; q += 32) {
+                                V3<R> v = P.v[q];
+                                o |= v.x * pn.x + v.y * pn.y + v.z * pn.z - pn.w > R(0);
+                            }
+                            if (__any_sync(FULLMASK, o)) {
+                                st |= CS_UNCERTIFIED;
+                                return false;
+                            }
+                        } else {
+                            int rc = poly_clip(P, pn, plen, j, lane, bad);
+                            if (rc == CLIP_EMPTY) {
+                                st |= CS_EMPTY;
+                                return false;
+                            }
+                            if (rc == CLIP_CAP) {
+                                st |= CS_CAPACITY;
+                                return false;
+                            }
+                            if (rc == CLIP_CUT) Rz = (float)poly_radius(P, zr, lane) * 1.0001f + 1e-6f;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    return true;
+}
+
+// Integrate the polytope and write the outputs of cell i.
+template <typename R>
+__device__ void integrate(WarpPoly<R>& P, const ClipParams& cp, int64_t i, int lane,
+                          bool& bad, uint32_t& st) {
+    double vol6 = 0, mx = 0, my = 0, mz = 0, sx = 0, sy = 0, sz = 0, sabs = 0;
+    int nf = 0;
+    int32_t fj[2];
+    double fc[2];
+    const int nt = P.nt;
+    for (int f = lane; f < ((P.np + 31) / 32) * 32; f += 32) {
+        // faces f are handled in rounds so every lane runs the same triangle loop
+        uint32_t ent[MAXFV];
+        int m = 0;
+        bool active = f < P.np;
+        for (int s = 0; s < nt; s++) {
+            uint32_t t = P.tri[s];
+            if (!active) continue;
+            uint32_t a = t & 0xff, b = (t >> 8) & 0xff, c = (t >> 16) & 0xff;
+            uint32_t x, y;
+            if (a == (uint32_t)f) { x = b; y = c; }
+            else if (b == (uint32_t)f) { x = c; y = a; }
+            else if (c == (uint32_t)f) { x = a; y = b; }
+            else continue;
+            if (m < MAXFV) ent[m] = x | (y << 8) | ((uint32_t)s << 16);
+            m++;
+        }
+        if (!active || m == 0) continue;
+        if (m > MAXFV) {
+            st |= CS_CAPACITY;
+            continue;
+        }
+        if (m < 3) {
+            bad = true;
+            continue;
+        }
+        // walk the cycle: the entry after (x, y) is the one whose x equals y
+        int cur = 0;
+        V3<R> v0 = P.v[ent[0] >> 16];
+        V3<R> vp = v0;
+        R Sx = 0, Sy = 0, Sz = 0;
+        bool ok = true;
+        for (int step = 1; step < m; step++) {
+            uint32_t yv = (ent[cur] >> 8) & 0xff;
+            int nxt = -1;
+            for (int e2 = 0; e2 < m; e2++)
+                if ((ent[e2] & 0xff) == yv) { nxt = e2; break; }
+            if (nxt < 0 || nxt == 0) { ok = false; break; }
+            cur = nxt;
+            V3<R> vc = P.v[ent[cur] >> 16];
+            if (step >= 2) {
+                // fan triangle (v0, vp, vc) and tetrahedron (0, v0, vp, vc)
+                R ax = vp.x - v0.x, ay = vp.y - v0.y, az = vp.z - v0.z;
+                R bx = vc.x - v0.x, by = vc.y - v0.y, bz = vc.z - v0.z;
+                R cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;
+                Sx += cx;
+                Sy += cy;
+                Sz += cz;
+                // det(v0, vp, vc) = v0 . (vp x vc) = v0 . ((vp - v0) x (vc - v0))
+                double d6 = (double)(v0.x * cx + v0.y * cy + v0.z * cz);
+                vol6 += d6;
+                mx += d6 * ((double)v0.x + (double)vp.x + (double)vc.x);
+                my += d6 * ((double)v0.y + (double)vp.y + (double)vc.y);
+                mz += d6 * ((double)v0.z + (double)vp.z + (double)vc.z);
+            }
+            vp = vc;
+        }
+        if (ok && ((ent[cur] >> 8) & 0xff) != (ent[0] & 0xff)) ok = false;
+        if (!ok) {
+            bad = true;
+            continue;
+        }
+        double ax2 = 0.5 * (double)Sx, ay2 = 0.5 * (double)Sy, az2 = 0.5 * (double)Sz;
+        double A = sqrt(ax2 * ax2 + ay2 * ay2 + az2 * az2);
+        sx += ax2;
+        sy += ay2;
+        sz += az2;
+        sabs += A;
+        int32_t j = P.pj[f];
+        if (j >= 0 && A > 0.0) {
+            if (nf < 2) {
+                fj[nf] = j;
+                fc[nf] = A * cp.a / (double)P.plen[f];
+            }
+            nf++;
+        }
+    }
+    vol6 = warp_sum(vol6);
+    mx = warp_sum(mx);
+    my = warp_sum(my);
+    mz = warp_sum(mz);
+    sx = warp_sum(sx);
+    sy = warp_sum(sy);
+    sz = warp_sum(sz);
+    sabs = warp_sum(sabs);
+    // facets
+    int incl = nf;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(FULLMASK, incl, o);
+        if (lane >= o) incl += y;
+    }
+    int total = __shfl_sync(FULLMASK, incl, 31);
+    if (total > FCAP) st |= CS_CAPACITY;
+    else {
+        int pos = incl - nf;
+        for (int q = 0; q < nf && q < 2; q++) {
+            cp.fcol[i * FCAP + pos + q] = fj[q];
+            cp.fval[i * FCAP + pos + q] = fc[q];
+        }
+    }
+    double closure = sqrt(sx * sx + sy * sy + sz * sz);
+    double tol = sizeof(R) == 4 ? 1e-4 : 1e-10;
+    if (!(closure <= tol * sabs)) bad = true;
+    double vol = vol6 / 6.0;
+    if (!(vol > 0.0) || !isfinite(vol)) bad = true;
+    bad = __any_sync(FULLMASK, bad);
+    uint32_t stall = __reduce_or_sync(FULLMASK, st);
+    st = stall;
+    if (lane == 0) {
+        double a3 = cp.a * cp.a * cp.a;
+        double a4 = a3 * cp.a;
+        double mm[3] = {mx / 24.0, my / 24.0, mz / 24.0};
+        cp.vol[i] = vol * a3;
+        cp.m1[3 * i + 0] = mm[0] * a4;
+        cp.m1[3 * i + 1] = mm[1] * a4;
+        cp.m1[3 * i + 2] = mm[2] * a4;
+        cp.fcnt[i] = total > FCAP ? FCAP : total;
+        if (vol > 0.0 && isfinite(vol)) {
+            cp.anchor[3 * i + 0] = (float)(mm[0] / vol);
+            cp.anchor[3 * i + 1] = (float)(mm[1] / vol);
+            cp.anchor[3 * i + 2] = (float)(mm[2] / vol);
+        }
+    }
+}
+
+template <typename R, int MODE>
+__global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
+    clip_kernel(ClipParams cp) {
+    __shared__ WarpPoly<R> polys[WARPS_PER_BLOCK];
+    const int lane = threadIdx.x & 31;
+    WarpPoly<R>& P = polys[threadIdx.x >> 5];
+    // global upper bound of psi (top pyramid level)
+    float psimax_glob = -INFINITY;
+    {
+        int tl = cp.pyr.nlev - 1;
+        int nt = cp.pyr.dim[tl][0] * cp.pyr.dim[tl][1] * cp.pyr.dim[tl][2];
+        for (int t = lane; t < nt; t += 32) psimax_glob = fmaxf(psimax_glob, cp.pyr.psimax[cp.pyr.off[tl] + t]);
+        psimax_glob = warp_max(psimax_glob);
+    }
+    const float halfLmin = 0.5f * fminf(cp.Lt[0], fminf(cp.Lt[1], cp.Lt[2]));
+    while (true) {
+        int64_t w = 0;
+        if (lane == 0) w = atomicAdd(cp.work_counter, 1);
+        w = __shfl_sync(FULLMASK, w, 0);
+        if (w >= cp.nwork) break;
+        const int64_t i = cp.worklist ? cp.worklist[w] : w;
+        const Pos4 yi = cp.pos[i];
+        const double psii = cp.psi[i];
+        bool bad = false;
+        uint32_t st = 0;
+        poly_init(P, cp, lane);
+        // k nearest neighbours: each lane builds one plane in FP64, then all clip
+        int emptied = 0;
+        for (int t0 = 0; t0 < cp.k; t0 += 32) {
+            int t = t0 + lane;
+            double nxd = 0, nyd = 0, nzd = 0, wd = 0;
+            int32_t j = -1;
+            if (t < cp.k) {
+                j = cp.knn[i * cp.k + t];
+                make_plane(cp, yi, psii, j, nxd, nyd, nzd, wd);
+            }
+            int nk = min(32, cp.k - t0);
+            for (int u = 0; u < nk; u++) {
+                V4<R> pn;
+                pn.x = (R)__shfl_sync(FULLMASK, nxd, u);
+                pn.y = (R)__shfl_sync(FULLMASK, nyd, u);
+                pn.z = (R)__shfl_sync(FULLMASK, nzd, u);
+                pn.w = (R)__shfl_sync(FULLMASK, wd, u);
+                int32_t ju = __shfl_sync(FULLMASK, j, u);
+                R plen = sqrt(pn.x * pn.x + pn.y * pn.y + pn.z * pn.z);
+                int rc = poly_clip(P, pn, plen, ju, lane, bad);
+                if (rc == CLIP_EMPTY) { emptied = 1; break; }
+                if (rc == CLIP_CAP) { st |= CS_CAPACITY; break; }
+            }
+            if (emptied || (st & CS_CAPACITY)) break;
+        }
+        if (emptied) st |= CS_EMPTY;
+        if (!st) {
+            Anchor an;
+            float4 yf = cp.posf[i];
+            an.yabs[0] = yf.x;
+            an.yabs[1] = yf.y;
+            an.yabs[2] = yf.z;
+            an.psi_i = yf.w;
+            float z0 = cp.anchor[3 * i], z1 = cp.anchor[3 * i + 1], z2 = cp.anchor[3 * i + 2];
+            if (!(isfinite(z0) && isfinite(z1) && isfinite(z2))) z0 = z1 = z2 = 0.f;
+            an.z[0] = z0;
+            an.z[1] = z1;
+            an.z[2] = z2;
+            an.z2h = 0.5f * (z0 * z0 + z1 * z1 + z2 * z2);
+            for (int a = 0; a < 3; a++) {
+                float za = an.yabs[a] + an.z[a];
+                za = fmodf(za, cp.Lt[a]);
+                if (za < 0.f) za += cp.Lt[a];
+                if (za >= cp.Lt[a]) za = 0.f;
+                an.zabs[a] = za;
+            }
+            double d2k = cp.knn_d2k[i];
+            int okk = (int)cp.pos[cp.knn[i * cp.k + cp.k - 1]].w;
+            bool done = traverse<R, MODE>(P, cp, i, yi, psii, an, d2k, okk, lane, bad, st);
+            if (!done && MODE == MODE_CERTIFY && (st & CS_UNCERTIFIED)) {
+                if (lane == 0) {
+                    int32_t q = atomicAdd(cp.queue_cnt, 1);
+                    cp.queue_out[q] = (int32_t)i;
+                    cp.status[i] = (uint8_t)st;
+                }
+                continue;
+            }
+        }
+        if (!st) {
+            // the cell must stay inside the minimum-image range of every other seed
+            V3<R> z0;
+            z0.x = z0.y = z0.z = R(0);
+            float R0 = (float)poly_radius(P, z0, lane);
+            float dpsi = fmaxf(psimax_glob - cp.posf[i].w, 0.f);
+            if (R0 + sqrtf(R0 * R0 + 2.f * dpsi) > halfLmin * 0.9999f) st |= CS_TOO_LARGE;
+        }
+        if (!(st & (CS_EMPTY | CS_CAPACITY))) integrate(P, cp, i, lane, bad, st);
+        if (bad) st |= CS_INCONSISTENT;
+        if (lane == 0) {
+            if (st & CS_EMPTY) {
+                cp.vol[i] = 0.0;
+                cp.m1[3 * i] = cp.m1[3 * i + 1] = cp.m1[3 * i + 2] = 0.0;
+                cp.fcnt[i] = 0;
+            }
+            cp.status[i] = (uint8_t)st;
+            bool redo = sizeof(R) == 4 && (st & (CS_INCONSISTENT | CS_CAPACITY));
+            if (redo) {
+                int32_t q = atomicAdd(cp.q64_cnt, 1);
+                cp.q64_out[q] = (int32_t)i;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// per-evaluation preparation: normalised float positions and the psi pyramid
+// ---------------------------------------------------------------------------
+__global__ void posf_kernel(const Pos4* __restrict__ pos, const double* __restrict__ psi,
+                            int64_t N, double inv_a, double inv_a2, float4* __restrict__ posf) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    Pos4 y = pos[s];
+    posf[s] = make_float4((float)(y.x * inv_a), (float)(y.y * inv_a), (float)(y.z * inv_a),
+                          (float)(psi[s] * inv_a2));
+}
+
+__global__ void leaf_max_kernel(const int32_t* __restrict__ cell_start, int64_t ncell,
+                                const double* __restrict__ psi, double inv_a2,
+                                float* __restrict__ out) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    int32_t b = cell_start[c], e = cell_start[c + 1];
+    double m = -INFINITY;
+    for (int32_t s = b; s < e; s++) m = fmax(m, psi[s]);
+    out[c] = (b == e) ? -INFINITY : __double2float_ru(m * inv_a2 * (1.0 + 1e-15 * (m > 0 ? 1 : -1)));
+}
+
+__global__ void level_max_kernel(const float* __restrict__ in, int dx, int dy, int dz,
+                                 float* __restrict__ out, int ox, int oy, int oz) {
+    int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= (int64_t)ox * oy * oz) return;
+    int X = (int)(n % ox), Y = (int)((n / ox) % oy), Z = (int)(n / ((int64_t)ox * oy));
+    float m = -INFINITY;
+    for (int c = 0; c < 64; c++) {
+        int x = 4 * X + (c & 3), y = 4 * Y + ((c >> 2) & 3), z = 4 * Z + (c >> 4);
+        if (x < dx && y < dy && z < dz) m = fmaxf(m, in[((int64_t)z * dy + y) * dx + x]);
+    }
+    out[n] = m;
+}
+
+int build_pyramid(DeviceState& d, const double* psi, cudaStream_t s) {
+    const int64_t N = d.N;
+    posf_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(d.pos, psi, N, 1.0 / d.a,
+                                                          1.0 / (d.a * d.a), d.posf);
+    SDOT_CUDA_TRY(cudaGetLastError());
+    Pyramid& P = d.pyr;
+    leaf_max_kernel<<<(unsigned)((d.grid.ncell + 255) / 256), 256, 0, s>>>(
+        d.grid.cell_start, d.grid.ncell, psi, 1.0 / (d.a * d.a), P.psimax + P.off[0]);
+    SDOT_CUDA_TRY(cudaGetLastError());
+    for (int l = 1; l < P.nlev; l++) {
+        int64_t n = (int64_t)P.dim[l][0] * P.dim[l][1] * P.dim[l][2];
+        level_max_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+            P.psimax + P.off[l - 1], P.dim[l - 1][0], P.dim[l - 1][1], P.dim[l - 1][2],
+            P.psimax + P.off[l], P.dim[l][0], P.dim[l][1], P.dim[l][2]);
+        SDOT_CUDA_TRY(cudaGetLastError());
+    }
+    return SDOT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// reductions over the cells
+// ---------------------------------------------------------------------------
+constexpr int RED_BLOCKS = 256;
+
+__global__ void cell_reduce_kernel(const double* __restrict__ vol, const double* __restrict__ nu,
+                                   const uint8_t* __restrict__ status, int64_t N,
+                                   double* __restrict__ part) {
+    double sv = 0, mr = 0, l2 = 0, mv = INFINITY, ne = 0;
+    uint32_t fl = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double v = vol[i], g = nu[i] - v;
+        sv += v;
+        mr = fmax(mr, fabs(g) / nu[i]);
+        l2 += g * g;
+        mv = fmin(mv, v);
+        if (!(v > 0)) ne += 1;
+        fl |= status[i];
+    }
+    __shared__ double sh[6][8];
+    for (int o = 16; o > 0; o >>= 1) {
+        sv += __shfl_xor_sync(FULLMASK, sv, o);
+        mr = fmax(mr, __shfl_xor_sync(FULLMASK, mr, o));
+        l2 += __shfl_xor_sync(FULLMASK, l2, o);
+        mv = fmin(mv, __shfl_xor_sync(FULLMASK, mv, o));
+        ne += __shfl_xor_sync(FULLMASK, ne, o);
+        fl |= __shfl_xor_sync(FULLMASK, fl, o);
+    }
+    int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        sh[0][w] = sv;
+        sh[1][w] = mr;
+        sh[2][w] = l2;
+        sh[3][w] = mv;
+        sh[4][w] = ne;
+        sh[5][w] = (double)fl;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int u = 1; u < (int)(blockDim.x >> 5); u++) {
+            sh[0][0] += sh[0][u];
+            sh[1][0] = fmax(sh[1][0], sh[1][u]);
+            sh[2][0] += sh[2][u];
+            sh[3][0] = fmin(sh[3][0], sh[3][u]);
+            sh[4][0] += sh[4][u];
+            sh[5][0] = (double)((uint32_t)sh[5][0] | (uint32_t)sh[5][u]);
+        }
+        for (int q = 0; q < 6; q++) part[blockIdx.x * 6 + q] = sh[q][0];
+    }
+}
+
+__global__ void cell_reduce_final(const double* __restrict__ part, int nb, double* __restrict__ out) {
+    if (threadIdx.x != 0) return;
+    double sv = 0, mr = 0, l2 = 0, mv = INFINITY, ne = 0;
+    uint32_t fl = 0;
+    for (int b = 0; b < nb; b++) {
+        sv += part[b * 6];
+        mr = fmax(mr, part[b * 6 + 1]);
+        l2 += part[b * 6 + 2];
+        mv = fmin(mv, part[b * 6 + 3]);
+        ne += part[b * 6 + 4];
+        fl |= (uint32_t)part[b * 6 + 5];
+    }
+    out[0] = sv;
+    out[1] = mr;
+    out[2] = sqrt(l2);
+    out[3] = mv;
+    out[4] = ne;
+    out[5] = (double)fl;
+}
+
+template <typename R, int MODE>
+static int launch_clip(const ClipParams& cp, cudaStream_t s) {
+    static int blocks = 0;
+    if (blocks == 0) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, clip_kernel<R, MODE>,
+                                                      WARPS_PER_BLOCK * 32, 0);
+        if (per_sm < 1) per_sm = 1;
+        blocks = per_sm * num_sms();
+    }
+    int64_t need = (cp.nwork + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
+    int nb = (int)(need < blocks ? need : blocks);
+    if (nb < 1) return SDOT_OK;
+    clip_kernel<R, MODE><<<nb, WARPS_PER_BLOCK * 32, 0, s>>>(cp);
+    SDOT_CUDA_TRY(cudaGetLastError());
+    return SDOT_OK;
+}
+
+int evaluate_cells(DeviceState& d, const double* psi, int precision, EvalResult* res,
+                   cudaStream_t s) {
+    int rc = build_pyramid(d, psi, s);
+    if (rc) return rc;
+    ClipParams cp;
+    cp.N = d.N;
+    cp.k = d.k;
+    cp.a = d.a;
+    cp.inv_a = 1.0 / d.a;
+    cp.inv_a2 = 1.0 / (d.a * d.a);
+    for (int a = 0; a < 3; a++) {
+        cp.L[a] = d.L[a];
+        cp.halfL[a] = 0.5 * d.L[a];
+        cp.Lt[a] = (float)(d.L[a] / d.a);
+        cp.halfLt[a] = 0.5f * cp.Lt[a];
+        cp.ht[a] = (float)(d.grid.h[a] / d.a);
+        cp.G[a] = d.grid.G[a];
+    }
+    cp.pos = d.pos;
+    cp.posf = d.posf;
+    cp.psi = psi;
+    cp.knn = d.knn;
+    cp.knn_d2k = d.knn_d2k;
+    cp.cell_start = d.grid.cell_start;
+    cp.pyr = d.pyr;
+    cp.vol = d.vol;
+    cp.m1 = d.m1;
+    cp.anchor = d.anchor;
+    cp.status = d.status;
+    cp.fcnt = d.fcnt;
+    cp.fcol = d.fcol;
+    cp.fval = d.fval;
+    cp.queue_out = d.queue;
+    cp.queue_cnt = d.counters + 0;
+    cp.q64_out = d.queue64;
+    cp.q64_cnt = d.counters + 1;
+    SDOT_CUDA_TRY(cudaMemsetAsync(d.counters, 0, 8 * sizeof(int32_t), s));
+
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    // pass 1: every cell, kNN planes + security test
+    cp.work_counter = d.counters + 2;
+    cp.worklist = nullptr;
+    cp.nwork = d.N;
+    rc = precision == SDOT_PREC_FP64 ? launch_clip<double, MODE_CERTIFY>(cp, s)
+                                     : launch_clip<float, MODE_CERTIFY>(cp, s);
+    if (rc) return rc;
+    int32_t cnt[2];
+    SDOT_CUDA_TRY(cudaMemcpyAsync(cnt, d.counters, 8, cudaMemcpyDeviceToHost, s));
+    SDOT_CUDA_TRY(cudaStreamSynchronize(s));
+    int64_t requeued = cnt[0];
+    // pass 2: re-queued cells, full walk with clipping
+    if (requeued > 0) {
+        cp.work_counter = d.counters + 4;
+        cp.worklist = d.queue;
+        cp.nwork = requeued;
+        rc = precision == SDOT_PREC_FP64 ? launch_clip<double, MODE_FULL>(cp, s)
+                                         : launch_clip<float, MODE_FULL>(cp, s);
+        if (rc) return rc;
+        SDOT_CUDA_TRY(cudaMemcpyAsync(cnt, d.counters, 8, cudaMemcpyDeviceToHost, s));
+        SDOT_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    int64_t reclipped = cnt[1];
+    // pass 3 (mixed): FP64 re-clip of cells failing the FP32 checks
+    if (precision != SDOT_PREC_FP64 && reclipped > 0) {
+        cp.work_counter = d.counters + 5;
+        cp.worklist = d.queue64;
+        cp.nwork = reclipped;
+        rc = launch_clip<double, MODE_FULL>(cp, s);
+        if (rc) return rc;
+    }
+    cudaEventRecord(e1, s);
+    cell_reduce_kernel<<<RED_BLOCKS, 256, 0, s>>>(d.vol, d.nu, d.status, d.N, d.partials);
+    SDOT_CUDA_TRY(cudaGetLastError());
+    cell_reduce_final<<<1, 32, 0, s>>>(d.partials, RED_BLOCKS, d.scal);
+    SDOT_CUDA_TRY(cudaGetLastError());
+    double h[6];
+    SDOT_CUDA_TRY(cudaMemcpyAsync(h, d.scal, sizeof h, cudaMemcpyDeviceToHost, s));
+    SDOT_CUDA_TRY(cudaStreamSynchronize(s));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    res->sum_vol = h[0];
+    res->max_rel_err = h[1];
+    res->l2_err = h[2];
+    res->min_vol = h[3];
+    res->n_empty = (int64_t)h[4];
+    res->flags = (uint32_t)h[5];
+    res->requeued = requeued;
+    res->reclipped = reclipped;
+    res->ms = ms;
+    return SDOT_OK;
+}
+
+}  // namespace sdot

@@ -1,0 +1,170 @@
+// Internal definitions shared by the CUDA translation units of libsdot.
+// Nothing here is part of the public ABI (include/sdot.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "sdot.h"
+
+namespace sdot {
+
+// one seed position, 32-byte aligned so a load is one sector; w = caller index
+struct __align__(32) Pos4 {
+    double x, y, z, w;
+    __host__ __device__ static Pos4 make(double x, double y, double z, double w) {
+        Pos4 p;
+        p.x = x;
+        p.y = y;
+        p.z = z;
+        p.w = w;
+        return p;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// capacities
+// ---------------------------------------------------------------------------
+constexpr int KMAX = 64;        // largest kNN size
+constexpr int MAXP = 64;        // planes per polytope (6 box planes included)
+constexpr int MAXT = 128;       // vertices (dual triangles) per polytope
+constexpr int FCAP = 48;        // facets stored per cell for the Hessian
+constexpr int MAXFV = 32;       // vertices per face during integration
+constexpr int STACK = 256;      // traversal stack entries per warp
+constexpr int MAXLEV = 8;       // pyramid levels
+constexpr int WARPS_PER_BLOCK = 4;
+
+// cell status bits (per cell, uint8)
+enum : uint32_t {
+    CS_OK = 0,
+    CS_EMPTY = 1,          // polytope vanished
+    CS_CAPACITY = 2,       // plane/vertex/facet/stack capacity exceeded
+    CS_INCONSISTENT = 4,   // FP32 consistency check failed
+    CS_UNCERTIFIED = 8,    // security test found a possible unseen cutter
+    CS_TOO_LARGE = 16,     // cell reaches a non-minimum periodic image
+};
+
+// ---------------------------------------------------------------------------
+// device data of one context (all arrays in grid-sorted seed order unless noted)
+// ---------------------------------------------------------------------------
+struct Pyramid {
+    int nlev;
+    int dim[MAXLEV][3];       // nodes per axis at each level (level 0 = grid cells)
+    int64_t off[MAXLEV];      // offset of each level in psimax
+    float* psimax;            // upper bound of psi/a^2 over the node (rounded up)
+};
+
+struct Grid {
+    int G[3];                 // grid cells per axis
+    double h[3];              // cell size per axis (absolute units)
+    int64_t ncell;
+    int32_t* cell_start;      // ncell + 1
+};
+
+struct DeviceState {
+    int64_t N;
+    int k;
+    double L[3];
+    double a;                 // length unit: (|box| / N)^(1/3)
+    // seeds
+    Pos4* pos;             // sorted positions; w = caller index (exact in fp64)
+    float4* posf;             // (x/a, y/a, z/a, psi/a^2), refreshed per evaluation
+    int32_t* perm;            // sorted -> caller index
+    int32_t* iperm;           // caller -> sorted index
+    double* nu;               // masses (sorted)
+    double* psi;              // current psi (sorted)
+    double* psi_trial;        // line-search trial (sorted)
+    double* delta;            // Newton direction (sorted)
+    int32_t* knn;             // N * k sorted neighbour indices
+    double* knn_d2k;          // d^2 of the k-th neighbour (key of the seen set)
+    // cell outputs of the last evaluation
+    double* vol;              // N
+    double* m1;               // N * 3, int_{V} (q - y) dq  (absolute units)
+    float* anchor;            // N * 3, previous local centroid / a (traversal anchor)
+    uint8_t* status;          // N
+    int32_t* fcnt;            // N facet counts
+    int32_t* fcol;            // N * FCAP facet neighbours (sorted index)
+    double* fval;             // N * FCAP facet coefficients A/|d|
+    int32_t* queue;           // N, re-queued cells
+    int32_t* queue64;         // N, cells for the FP64 re-clip
+    int32_t* counters;        // [0] requeue count [1] fp64 count [2] work counter
+                              // [3] error flags [4] work counter 2 [5] work counter 3
+    // CSR (sorted order)
+    int64_t* row_ptr;         // N + 1
+    int32_t* col;             // nnz capacity N * (FCAP + 1)
+    double* val;
+    int32_t* rowcnt;          // N (+1 pad)
+    // CSR (caller order), built on demand for sdot_laguerre
+    int64_t* row_ptr_u;
+    int32_t* col_u;
+    double* val_u;
+    // PCG vectors
+    double *x, *r, *z, *p, *q, *dinv;
+    double* partials;         // reduction partials
+    double* scal;             // device scalars
+    Grid grid;
+    Pyramid pyr;
+};
+
+// ---------------------------------------------------------------------------
+// error handling
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+
+#define SDOT_CUDA_TRY(expr)                                                              \
+    do {                                                                                 \
+        cudaError_t e_ = (expr);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            ::sdot::set_error(std::string(#expr) + ": " + cudaGetErrorString(e_));       \
+            return SDOT_ERR_CUDA;                                                        \
+        }                                                                                \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// launchers (host functions defined in the .cu files)
+// ---------------------------------------------------------------------------
+int num_sms();
+
+// exclusive scans (in may alias out); temp must hold scan_temp_elems(n) elements
+size_t scan_temp_bytes(int64_t n);
+int scan_exclusive_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, void* temp,
+                              cudaStream_t s);
+int scan_exclusive_i32(const int32_t* in, int32_t* out, int64_t n, void* temp,
+                       cudaStream_t s);
+
+// grid_knn.cu
+int build_grid(DeviceState& d, const double* pos_user_dev, double seeds_per_leaf,
+               void* temp, cudaStream_t s);
+int build_knn(DeviceState& d, cudaStream_t s, int* dup_flag_host);
+int knn_to_user(const DeviceState& d, int32_t* out_user_dev, cudaStream_t s);
+
+// clip.cu
+struct EvalResult {
+    double sum_vol, max_rel_err, l2_err, min_vol;
+    int64_t requeued, reclipped, n_empty;
+    uint32_t flags;
+    float ms;
+};
+int build_pyramid(DeviceState& d, const double* psi, cudaStream_t s);
+int evaluate_cells(DeviceState& d, const double* psi, int precision, EvalResult* res,
+                   cudaStream_t s);
+
+// linalg.cu
+int csr_count(DeviceState& d, int64_t* nnz_out, cudaStream_t s);  // row_ptr and nnz
+int csr_fill(DeviceState& d, cudaStream_t s);                      // col, val, dinv
+int assemble_csr_user(DeviceState& d, int64_t nnz, cudaStream_t s);
+int pcg_solve(DeviceState& d, double rtol, int maxit, int* iters, double* rel_res,
+              cudaStream_t s);
+int axpy_gauge(DeviceState& d, const double* psi, const double* delta, double alpha,
+               double* out, cudaStream_t s);
+int subtract_mean(DeviceState& d, double* v, cudaStream_t s);
+int scatter_to_user(const DeviceState& d, const double* sorted, double* user, int width,
+                    cudaStream_t s);
+int gather_from_user(const DeviceState& d, const double* user, double* sorted, int width,
+                     cudaStream_t s);
+int centroids_user(const DeviceState& d, double* out_user, int wrap_abs, cudaStream_t s);
+int check_masses(const DeviceState& d, double* sum_out, double* min_out, cudaStream_t s);
+
+}  // namespace sdot

@@ -1,0 +1,492 @@
+// Hessian assembly (CSR) and the Newton linear solve.
+//
+// The second derivative of K (eq. SDK; K is C^2 by the smoothness paragraph of Sec.
+// "Monge-Ampere-Kantorovich Reconstruction") is -L with L the weighted graph
+// Laplacian of the Laguerre diagram: L_ij = -A_ij/|d_ij| for every facet, L_ii =
+// -sum_j L_ij. Each cell reports its own facets; the matrix keeps the mean of the
+// two reports of a facet and drops facets seen by one side only (zero-area contacts
+// resolved differently by rounding), so L is exactly symmetric with zero row sums.
+//
+// The Newton direction solves L delta = nu - V (projected to mean zero: L is
+// singular with the constants as kernel) by Jacobi-preconditioned conjugate
+// gradients. Dot products use fixed-order two-level reductions (per-block partials
+// summed in block order by every consumer) so results are bitwise reproducible.
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace sdot {
+
+#define FULLMASK 0xffffffffu
+
+// ---------------------------------------------------------------------------
+// CSR assembly
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double sym_value(const int32_t* __restrict__ fcnt,
+                                            const int32_t* __restrict__ fcol,
+                                            const double* __restrict__ fval, int64_t i, int t) {
+    int32_t j = fcol[i * FCAP + t];
+    double c = fval[i * FCAP + t];
+    int n = fcnt[j];
+    for (int u = 0; u < n; u++)
+        if (fcol[(int64_t)j * FCAP + u] == (int32_t)i) return 0.5 * (c + fval[(int64_t)j * FCAP + u]);
+    return 0.0;
+}
+
+__global__ void csr_count_kernel(const int32_t* __restrict__ fcnt, const int32_t* __restrict__ fcol,
+                                 const double* __restrict__ fval, int64_t N,
+                                 int32_t* __restrict__ rowcnt) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int n = fcnt[i], kept = 0;
+    for (int t = 0; t < n; t++)
+        if (sym_value(fcnt, fcol, fval, i, t) > 0.0) kept++;
+    rowcnt[i] = kept + 1;
+}
+
+__global__ void csr_fill_kernel(const int32_t* __restrict__ fcnt, const int32_t* __restrict__ fcol,
+                                const double* __restrict__ fval, int64_t N,
+                                const int64_t* __restrict__ row_ptr, int32_t* __restrict__ col,
+                                double* __restrict__ val, double* __restrict__ dinv) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int n = fcnt[i];
+    int64_t p0 = row_ptr[i];
+    int64_t p = p0 + 1;
+    double diag = 0.0;
+    for (int t = 0; t < n; t++) {
+        double v = sym_value(fcnt, fcol, fval, i, t);
+        if (!(v > 0.0)) continue;
+        int32_t j = fcol[i * FCAP + t];
+        // insertion into the row, increasing column
+        int64_t q = p;
+        while (q > p0 + 1 && col[q - 1] > j) {
+            col[q] = col[q - 1];
+            val[q] = val[q - 1];
+            q--;
+        }
+        col[q] = j;
+        val[q] = -v;
+        p++;
+        diag += v;
+    }
+    col[p0] = (int32_t)i;
+    val[p0] = diag;
+    dinv[i] = diag > 0.0 ? 1.0 / diag : 0.0;
+}
+
+int csr_count(DeviceState& d, int64_t* nnz_out, cudaStream_t s) {
+    const int64_t N = d.N;
+    unsigned nb = (unsigned)((N + 255) / 256);
+    csr_count_kernel<<<nb, 256, 0, s>>>(d.fcnt, d.fcol, d.fval, N, d.rowcnt);
+    SDOT_CUDA_TRY(cudaGetLastError());
+    // row_ptr = exclusive scan over N+1 entries (rowcnt[N] == 0)
+    SDOT_CUDA_TRY(cudaMemsetAsync(d.rowcnt + N, 0, 4, s));
+    int rc = scan_exclusive_i32_to_i64(d.rowcnt, d.row_ptr, N + 1, d.partials + 4096, s);
+    if (rc) return rc;
+    int64_t nnz = 0;
+    SDOT_CUDA_TRY(cudaMemcpyAsync(&nnz, d.row_ptr + N, 8, cudaMemcpyDeviceToHost, s));
+    SDOT_CUDA_TRY(cudaStreamSynchronize(s));
+    *nnz_out = nnz;
+    return SDOT_OK;
+}
+
+int csr_fill(DeviceState& d, cudaStream_t s) {
+    const int64_t N = d.N;
+    unsigned nb = (unsigned)((N + 255) / 256);
+    csr_fill_kernel<<<nb, 256, 0, s>>>(d.fcnt, d.fcol, d.fval, N, d.row_ptr, d.col, d.val, d.dinv);
+    SDOT_CUDA_TRY(cudaGetLastError());
+    return SDOT_OK;
+}
+
+// the same matrix in the caller's index order
+__global__ void csr_user_count(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ perm,
+                               int64_t N, int32_t* __restrict__ cnt_user) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    cnt_user[perm[s]] = (int32_t)(row_ptr[s + 1] - row_ptr[s]);
+}
+
+__global__ void csr_user_fill(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                              const double* __restrict__ val, const int32_t* __restrict__ perm,
+                              int64_t N, const int64_t* __restrict__ rp_u,
+                              int32_t* __restrict__ col_u, double* __restrict__ val_u) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    int64_t b = row_ptr[s], e = row_ptr[s + 1];
+    int64_t o = rp_u[perm[s]];
+    col_u[o] = perm[col[b]];
+    val_u[o] = val[b];
+    int64_t p = o + 1;
+    for (int64_t t = b + 1; t < e; t++) {
+        int32_t j = perm[col[t]];
+        double v = val[t];
+        int64_t q = p;
+        while (q > o + 1 && col_u[q - 1] > j) {
+            col_u[q] = col_u[q - 1];
+            val_u[q] = val_u[q - 1];
+            q--;
+        }
+        col_u[q] = j;
+        val_u[q] = v;
+        p++;
+    }
+}
+
+int assemble_csr_user(DeviceState& d, int64_t nnz, cudaStream_t s) {
+    (void)nnz;
+    const int64_t N = d.N;
+    unsigned nb = (unsigned)((N + 255) / 256);
+    csr_user_count<<<nb, 256, 0, s>>>(d.row_ptr, d.perm, N, d.rowcnt);
+    SDOT_CUDA_TRY(cudaGetLastError());
+    SDOT_CUDA_TRY(cudaMemsetAsync(d.rowcnt + N, 0, 4, s));
+    int rc = scan_exclusive_i32_to_i64(d.rowcnt, d.row_ptr_u, N + 1, d.partials + 4096, s);
+    if (rc) return rc;
+    csr_user_fill<<<nb, 256, 0, s>>>(d.row_ptr, d.col, d.val, d.perm, N, d.row_ptr_u, d.col_u,
+                                     d.val_u);
+    SDOT_CUDA_TRY(cudaGetLastError());
+    return SDOT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// PCG
+// ---------------------------------------------------------------------------
+constexpr int PCG_THREADS = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULLMASK, v, o);
+    int w = threadIdx.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0;
+    if (threadIdx.x == 0)
+        for (int u = 0; u < (int)(blockDim.x >> 5); u++) t += sh[u];
+    return t;  // valid in thread 0
+}
+
+// fixed-order sum of nb partials with stride; every block gets the same value
+__device__ __forceinline__ double sum_partials(const double* __restrict__ part, int nb, int stride,
+                                               double* sh) {
+    double v = 0;
+    // each thread sums a fixed subset, then a fixed-order block reduction
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += part[(int64_t)b * stride];
+    double t = block_sum(v, sh);
+    __shared__ double bc;
+    if (threadIdx.x == 0) bc = t;
+    __syncthreads();
+    return bc;
+}
+
+// r = g - mean, x = 0, z = dinv r, p = z; partials (r.z, r.r) into partB
+__global__ void pcg_init_kernel(const double* __restrict__ nu, const double* __restrict__ vol,
+                                double mean, const double* __restrict__ dinv, int64_t N,
+                                double* __restrict__ x, double* __restrict__ r,
+                                double* __restrict__ z, double* __restrict__ p,
+                                double* __restrict__ partB) {
+    __shared__ double sh[32];
+    double rz = 0, rr = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double ri = (nu[i] - vol[i]) - mean;
+        double zi = dinv[i] * ri;
+        x[i] = 0.0;
+        r[i] = ri;
+        z[i] = zi;
+        p[i] = zi;
+        rz += ri * zi;
+        rr += ri * ri;
+    }
+    double a = block_sum(rz, sh);
+    double b = block_sum(rr, sh);
+    if (threadIdx.x == 0) {
+        partB[blockIdx.x * 2] = a;
+        partB[blockIdx.x * 2 + 1] = b;
+    }
+}
+
+// q = L p (8 lanes per row), partials of p.q into partA
+__global__ void pcg_spmv_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                const double* __restrict__ val, const double* __restrict__ p,
+                                int64_t N, double* __restrict__ q, double* __restrict__ partA) {
+    __shared__ double sh[32];
+    const int sub = threadIdx.x & 7;
+    double pq = 0;
+    const int64_t groups = (int64_t)gridDim.x * (blockDim.x >> 3);
+    const int64_t g0 = (int64_t)blockIdx.x * (blockDim.x >> 3) + (threadIdx.x >> 3);
+    const int64_t niter = (N + groups - 1) / groups;  // same for every lane
+    for (int64_t it = 0; it < niter; it++) {
+        const int64_t i = g0 + it * groups;
+        double acc = 0;
+        if (i < N) {
+            int64_t b = row_ptr[i], e = row_ptr[i + 1];
+            for (int64_t t = b + sub; t < e; t += 8) acc += val[t] * p[col[t]];
+        }
+        acc += __shfl_xor_sync(FULLMASK, acc, 4);
+        acc += __shfl_xor_sync(FULLMASK, acc, 2);
+        acc += __shfl_xor_sync(FULLMASK, acc, 1);
+        if (sub == 0 && i < N) {
+            q[i] = acc;
+            pq += acc * p[i];
+        }
+    }
+    double a = block_sum(pq, sh);
+    if (threadIdx.x == 0) partA[blockIdx.x] = a;
+}
+
+__global__ void pcg_update_kernel(const double* __restrict__ partA, const double* __restrict__ partB_prev,
+                                  double* __restrict__ partB_cur, int nb,
+                                  const double* __restrict__ dinv, int64_t N,
+                                  double* __restrict__ x, double* __restrict__ r,
+                                  double* __restrict__ z, const double* __restrict__ p,
+                                  const double* __restrict__ q) {
+    __shared__ double sh[32];
+    double pq = sum_partials(partA, nb, 1, sh);
+    double rz = sum_partials(partB_prev, nb, 2, sh);
+    double alpha = pq != 0.0 ? rz / pq : 0.0;
+    double rzn = 0, rr = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double xi = x[i] + alpha * p[i];
+        double ri = r[i] - alpha * q[i];
+        double zi = dinv[i] * ri;
+        x[i] = xi;
+        r[i] = ri;
+        z[i] = zi;
+        rzn += ri * zi;
+        rr += ri * ri;
+    }
+    double a = block_sum(rzn, sh);
+    double b = block_sum(rr, sh);
+    if (threadIdx.x == 0) {
+        partB_cur[blockIdx.x * 2] = a;
+        partB_cur[blockIdx.x * 2 + 1] = b;
+    }
+}
+
+__global__ void pcg_dir_kernel(const double* __restrict__ partB_prev,
+                               const double* __restrict__ partB_cur, int nb, int64_t N,
+                               const double* __restrict__ z, double* __restrict__ p) {
+    __shared__ double sh[32];
+    double rzo = sum_partials(partB_prev, nb, 2, sh);
+    double rzn = sum_partials(partB_cur, nb, 2, sh);
+    double beta = rzo != 0.0 ? rzn / rzo : 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = z[i] + beta * p[i];
+}
+
+__global__ void partial_final_kernel(const double* __restrict__ part, int nb, int stride, int off,
+                                     double* __restrict__ out) {
+    __shared__ double sh[32];
+    double v = sum_partials(part + off, nb, stride, sh);
+    if (threadIdx.x == 0) *out = v;
+}
+
+int pcg_solve(DeviceState& d, double rtol, int maxit, int* iters, double* rel_res,
+              cudaStream_t s) {
+    const int64_t N = d.N;
+    const int nb = 2 * num_sms();
+    double* partA = d.partials;
+    double* partB[2] = {d.partials + nb, d.partials + 3 * nb};
+    double* hs = d.scal + 8;
+    // mean of g = nu - V (its sum is rounding noise when sum nu = |box|)
+    // computed on the host from the last evaluation reduction: scal[0] holds sum V
+    double sums[1];
+    SDOT_CUDA_TRY(cudaMemcpyAsync(sums, d.scal, 8, cudaMemcpyDeviceToHost, s));
+    SDOT_CUDA_TRY(cudaStreamSynchronize(s));
+    double box = d.L[0] * d.L[1] * d.L[2];
+    double mean = (box - sums[0]) / (double)N;
+    pcg_init_kernel<<<nb, PCG_THREADS, 0, s>>>(d.nu, d.vol, mean, d.dinv, N, d.x, d.r, d.z, d.p,
+                                               partB[1]);
+    SDOT_CUDA_TRY(cudaGetLastError());
+    double h[2];
+    partial_final_kernel<<<1, PCG_THREADS, 0, s>>>(partB[1], nb, 2, 1, hs);
+    SDOT_CUDA_TRY(cudaMemcpyAsync(h, hs, 8, cudaMemcpyDeviceToHost, s));
+    SDOT_CUDA_TRY(cudaStreamSynchronize(s));
+    const double rr0 = h[0];
+    *iters = 0;
+    *rel_res = 0.0;
+    if (!(rr0 > 0.0)) return SDOT_OK;
+    const double thr = rtol * rtol * rr0;
+    const int check = 8;
+    int it = 0;
+    double rr = rr0;
+    while (it < maxit) {
+        for (int c = 0; c < check && it < maxit; c++, it++) {
+            double* prev = partB[(it + 1) & 1];
+            double* cur = partB[it & 1];
+            pcg_spmv_kernel<<<nb, PCG_THREADS, 0, s>>>(d.row_ptr, d.col, d.val, d.p, N, d.q, partA);
+            pcg_update_kernel<<<nb, PCG_THREADS, 0, s>>>(partA, prev, cur, nb, d.dinv, N, d.x, d.r,
+                                                         d.z, d.p, d.q);
+            pcg_dir_kernel<<<nb, PCG_THREADS, 0, s>>>(prev, cur, nb, N, d.z, d.p);
+        }
+        SDOT_CUDA_TRY(cudaGetLastError());
+        partial_final_kernel<<<1, PCG_THREADS, 0, s>>>(partB[(it - 1) & 1], nb, 2, 1, hs);
+        SDOT_CUDA_TRY(cudaMemcpyAsync(h, hs, 8, cudaMemcpyDeviceToHost, s));
+        SDOT_CUDA_TRY(cudaStreamSynchronize(s));
+        rr = h[0];
+        if (!(rr > thr)) break;
+    }
+    *iters = it;
+    *rel_res = sqrt(rr / rr0);
+    return SDOT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// vector helpers
+// ---------------------------------------------------------------------------
+__global__ void axpy_kernel(const double* __restrict__ a, const double* __restrict__ b,
+                            double alpha, int64_t N, double* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) out[i] = a[i] + alpha * b[i];
+}
+
+int axpy_gauge(DeviceState& d, const double* psi, const double* delta, double alpha, double* out,
+               cudaStream_t s) {
+    axpy_kernel<<<(unsigned)((d.N + 255) / 256), 256, 0, s>>>(psi, delta, alpha, d.N, out);
+    SDOT_CUDA_TRY(cudaGetLastError());
+    return SDOT_OK;
+}
+
+__global__ void sum_kernel(const double* __restrict__ v, int64_t N, double* __restrict__ part) {
+    __shared__ double sh[32];
+    double t = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x)
+        t += v[i];
+    double a = block_sum(t, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = a;
+}
+
+__global__ void sub_mean_kernel(double* __restrict__ v, int64_t N, const double* __restrict__ part,
+                                int nb) {
+    __shared__ double sh[32];
+    double m = sum_partials(part, nb, 1, sh) / (double)N;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x)
+        v[i] -= m;
+}
+
+int subtract_mean(DeviceState& d, double* v, cudaStream_t s) {
+    const int nb = 2 * num_sms();
+    sum_kernel<<<nb, 256, 0, s>>>(v, d.N, d.partials);
+    sub_mean_kernel<<<nb, 256, 0, s>>>(v, d.N, d.partials, nb);
+    SDOT_CUDA_TRY(cudaGetLastError());
+    return SDOT_OK;
+}
+
+__global__ void scatter_kernel_w(const double* __restrict__ in, const int32_t* __restrict__ perm,
+                                 int64_t N, int w, double* __restrict__ out) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N * w) return;
+    int64_t s = t / w;
+    int c = (int)(t - s * w);
+    out[(int64_t)perm[s] * w + c] = in[t];
+}
+
+__global__ void gather_kernel_w(const double* __restrict__ in, const int32_t* __restrict__ perm,
+                                int64_t N, int w, double* __restrict__ out) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N * w) return;
+    int64_t s = t / w;
+    int c = (int)(t - s * w);
+    out[t] = in[(int64_t)perm[s] * w + c];
+}
+
+int scatter_to_user(const DeviceState& d, const double* sorted, double* user, int w,
+                    cudaStream_t s) {
+    int64_t n = d.N * w;
+    scatter_kernel_w<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sorted, d.perm, d.N, w, user);
+    SDOT_CUDA_TRY(cudaGetLastError());
+    return SDOT_OK;
+}
+
+int gather_from_user(const DeviceState& d, const double* user, double* sorted, int w,
+                     cudaStream_t s) {
+    int64_t n = d.N * w;
+    gather_kernel_w<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(user, d.perm, d.N, w, sorted);
+    SDOT_CUDA_TRY(cudaGetLastError());
+    return SDOT_OK;
+}
+
+// wrap_abs = 1: absolute centroid wrapped into the box; 0: displacement y - c = -m1/V
+__global__ void centroid_kernel(const Pos4* __restrict__ pos, const double* __restrict__ m1,
+                                const double* __restrict__ vol, const int32_t* __restrict__ perm,
+                                int64_t N, double Lx, double Ly, double Lz, int wrap_abs,
+                                double* __restrict__ out) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    double v = vol[s];
+    double c[3] = {0, 0, 0};
+    if (v > 0) {
+        c[0] = m1[3 * s] / v;
+        c[1] = m1[3 * s + 1] / v;
+        c[2] = m1[3 * s + 2] / v;
+    }
+    int64_t o = (int64_t)perm[s] * 3;
+    if (wrap_abs) {
+        Pos4 y = pos[s];
+        double L[3] = {Lx, Ly, Lz};
+        double q[3] = {y.x + c[0], y.y + c[1], y.z + c[2]};
+        for (int a = 0; a < 3; a++) {
+            double t = fmod(q[a], L[a]);
+            if (t < 0) t += L[a];
+            if (t >= L[a]) t -= L[a];
+            out[o + a] = t;
+        }
+    } else {
+        out[o] = -c[0];
+        out[o + 1] = -c[1];
+        out[o + 2] = -c[2];
+    }
+}
+
+int centroids_user(const DeviceState& d, double* out, int wrap_abs, cudaStream_t s) {
+    centroid_kernel<<<(unsigned)((d.N + 255) / 256), 256, 0, s>>>(
+        d.pos, d.m1, d.vol, d.perm, d.N, d.L[0], d.L[1], d.L[2], wrap_abs, out);
+    SDOT_CUDA_TRY(cudaGetLastError());
+    return SDOT_OK;
+}
+
+__global__ void mass_kernel(const double* __restrict__ nu, int64_t N, double* __restrict__ part) {
+    __shared__ double sh[32];
+    double t = 0, mn = INFINITY;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double v = nu[i];
+        t += v;
+        mn = fmin(mn, isfinite(v) ? v : -INFINITY);
+    }
+    double a = block_sum(t, sh);
+    for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_xor_sync(FULLMASK, mn, o));
+    __shared__ double mm[32];
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) mm[threadIdx.x >> 5] = mn;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = INFINITY;
+        for (int u = 0; u < (int)(blockDim.x >> 5); u++) m = fmin(m, mm[u]);
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = m;
+    }
+}
+
+int check_masses(const DeviceState& d, double* sum_out, double* min_out, cudaStream_t s) {
+    const int nb = 64;
+    mass_kernel<<<nb, 256, 0, s>>>(d.nu, d.N, d.partials);
+    SDOT_CUDA_TRY(cudaGetLastError());
+    double h[2 * nb];
+    SDOT_CUDA_TRY(cudaMemcpyAsync(h, d.partials, sizeof h, cudaMemcpyDeviceToHost, s));
+    SDOT_CUDA_TRY(cudaStreamSynchronize(s));
+    double t = 0, m = INFINITY;
+    for (int b = 0; b < nb; b++) {
+        t += h[2 * b];
+        m = fmin(m, h[2 * b + 1]);
+    }
+    *sum_out = t;
+    *min_out = m;
+    return SDOT_OK;
+}
+
+}  // namespace sdot

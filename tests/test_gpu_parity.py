@@ -1,0 +1,189 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances (from the arithmetic, stated here once):
+  * kNN lists: bit-exact (integer result of an exact FP64 key).
+  * FP64 volumes / centroids: 1e-10 relative (to a^3 / a); Hessian entries 1e-10 of the
+    row diagonal.
+  * Mixed precision (FP32 geometry in units of the spacing a, FP64 sums): volumes 2e-5
+    relative, centroids 2e-5 a, Hessian 2e-4 of the diagonal; the solve reaches the same
+    max|V - nu|/nu criterion.
+  * Displacement at convergence (both sides solved to 1e-10): 1e-6 a.
+"""
+import numpy as np
+import pytest
+
+import sdot_oracle as O
+from paper_2110_08868_gb300 import ics
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2110_08868_gb300 import binding as B  # noqa: E402
+
+
+def c1():
+    return ics.make_config(**ics.CONFIGS["zeldovich-16^3-kinv-0.3a"])
+
+
+def _hess_close(Lg, Lo, tol):
+    Lg = Lg.toarray() if hasattr(Lg, "toarray") else Lg
+    Lo = Lo.toarray() if hasattr(Lo, "toarray") else Lo
+    scale = np.abs(np.diag(Lo))[:, None]
+    return np.max(np.abs(Lg - Lo) / scale) <= tol, np.max(np.abs(Lg - Lo) / scale)
+
+
+def test_knn_bit_exact_c1():
+    y, nu, L = c1()
+    s = B.Solver(y, [L] * 3, precision="fp64")
+    nb = s.knn()
+    ref, _ = O.knn(y, L, 24)
+    np.testing.assert_array_equal(nb, ref)
+
+
+@pytest.mark.parametrize("k", [8, 24, 33])
+def test_knn_bit_exact_ties_and_ragged(k):
+    # 7^3 lattice (many exact ties) plus 17 extra random points (ragged N)
+    rng = np.random.default_rng(4)
+    q = ics.lattice(7, 1.0)
+    y = np.concatenate([q, rng.uniform(0, 1, (17, 3))])
+    s = B.Solver(y, [1.0] * 3, precision="fp64", k=k)
+    ref, _ = O.knn(y, 1.0, k)
+    np.testing.assert_array_equal(s.knn(), ref)
+
+
+@pytest.mark.parametrize("prec,vtol,ctol,htol", [("fp64", 1e-10, 1e-10, 1e-10),
+                                                  ("mixed", 2e-5, 2e-5, 2e-4)])
+def test_laguerre_psi0_c1(prec, vtol, ctol, htol):
+    y, nu, L = c1()
+    N = y.shape[0]
+    a = L / 16
+    s = B.Solver(y, [L] * 3, precision=prec)
+    g = s.laguerre(with_hessian=True)
+    o = O.laguerre(y, np.zeros(N), L, nu)
+    np.testing.assert_allclose(g["vol"], o["vol"], rtol=0, atol=vtol * a ** 3)
+    dc = g["centroid"] - o["centroid"]
+    dc -= L * np.round(dc / L)
+    assert np.max(np.abs(dc)) <= ctol * a
+    ok, err = _hess_close(g["hess"], o["L"], htol)
+    assert ok, err
+
+
+@pytest.mark.parametrize("prec,vtol,htol", [("fp64", 1e-10, 1e-10), ("mixed", 2e-5, 2e-4)])
+def test_laguerre_random_psi_c1(prec, vtol, htol):
+    # a non-trivial psi (the oracle's Newton direction after one step) makes the
+    # cells leave their seeds, which exercises the security test and the re-queue
+    y, nu, L = c1()
+    N = y.shape[0]
+    a = L / 16
+    rng = np.random.default_rng(9)
+    psi = 0.2 * a * a * rng.standard_normal(N)
+    s = B.Solver(y, [L] * 3, precision=prec)
+    g = s.laguerre(psi, with_hessian=True, allow_empty=True)
+    o = O.laguerre(y, psi, L, nu)
+    np.testing.assert_allclose(g["vol"], o["vol"], rtol=0, atol=vtol * a ** 3)
+    ok, err = _hess_close(g["hess"], o["L"], htol)
+    assert ok, err
+
+
+def test_solve_fp64_matches_oracle_displacement():
+    y, nu, L = c1()
+    a = L / 16
+    s = B.Solver(y, [L] * 3, precision="fp64")
+    st = s.solve(1e-10)
+    assert st["max_rel_err"] <= 1e-10
+    psi_o, info = O.solve(y, nu, L, tol=1e-11)
+    d = s.displacement()
+    assert np.max(np.abs(d - info["disp"])) <= 1e-6 * a
+    np.testing.assert_allclose(s.psi(), psi_o, atol=1e-7 * a * a)
+
+
+def test_solve_mixed_reaches_criterion():
+    y, nu, L = c1()
+    a = L / 16
+    s = B.Solver(y, [L] * 3, precision="mixed")
+    st = s.solve(1e-4)
+    assert st["max_rel_err"] <= 1e-4
+    _, info = O.solve(y, nu, L, tol=1e-11)
+    err = np.max(np.abs(s.displacement() - info["disp"])) / a
+    # a 1e-4 volume stop leaves centroid errors of order 1e-5 a
+    assert err < 1e-3, err
+
+
+def test_lattice_zero_iterations():
+    n, L = 12, 3.0
+    y = ics.lattice(n, L)
+    s = B.Solver(y, [L] * 3, precision="fp64")
+    st = s.solve(1e-12)
+    assert st["newton_iters"] == 0
+    np.testing.assert_allclose(s.displacement(), 0.0, atol=1e-12 * L / n)
+
+
+def test_plane_wave_closed_form_gpu():
+    from test_oracle_pins import plane_wave
+
+    n, L = 24, 1.0
+    y, psi_exact, sdisp = plane_wave(n, L, [0.09, 0.05, 0.12], [0.3, 1.1, -0.4])
+    a = L / n
+    s = B.Solver(y, [L] * 3, precision="fp64")
+    g = s.laguerre(psi_exact)
+    np.testing.assert_allclose(g["vol"], a ** 3, rtol=1e-10)
+    st = s.solve(1e-11)
+    assert st["max_rel_err"] <= 1e-11
+    np.testing.assert_allclose(s.displacement(), sdisp, atol=1e-7 * a)
+
+
+def test_error_codes():
+    y, nu, L = c1()
+    opt = B.sdot_default_options()
+    rc, ctx = B.sdot_create(y, nu * 1.01, [L] * 3, opt)
+    assert rc == B.SDOT_ERR_MASS and not ctx
+    yd = y.copy()
+    yd[5] = yd[9]
+    rc, ctx = B.sdot_create(yd, None, [L] * 3, opt)
+    assert rc == B.SDOT_ERR_DUPLICATE
+    yo = y.copy()
+    yo[3, 0] = L
+    rc, ctx = B.sdot_create(yo, None, [L] * 3, opt)
+    assert rc == B.SDOT_ERR_ARG
+    rc, ctx = B.sdot_create(y[:10], None, [L] * 3, opt)
+    assert rc == B.SDOT_ERR_TOO_FEW
+    # a psi that empties a cell
+    s = B.Solver(y, [L] * 3, precision="fp64")
+    psi = np.zeros(y.shape[0])
+    psi[7] = -50 * (L / 16) ** 2
+    g = s.laguerre(psi, allow_empty=True)
+    assert g["rc"] == B.SDOT_ERR_EMPTY_CELL and g["vol"][7] == 0.0
+    assert abs(g["vol"].sum() - L ** 3) < 1e-10
+
+
+def test_device_pointers_and_stream():
+    y, nu, L = c1()
+    pos = torch.from_numpy(y).cuda()
+    stream = torch.cuda.Stream()
+    rc, ctx = B.sdot_create(pos, torch.from_numpy(nu).cuda(), [L] * 3,
+                            B.sdot_default_options(precision="fp64"))
+    B.check(rc)
+    try:
+        B.check(B.sdot_set_stream(ctx, stream))
+        vol = torch.empty(y.shape[0], dtype=torch.float64, device="cuda")
+        B.check(B.sdot_laguerre(ctx, None, vol, None, None))
+        o = O.laguerre(y, np.zeros(y.shape[0]), L, nu, with_hessian=False)
+        np.testing.assert_allclose(vol.cpu().numpy(), o["vol"], rtol=1e-10)
+    finally:
+        B.sdot_destroy(ctx)
+
+
+def test_c2_sampled_cells_fp64():
+    # full 128^3 box of the BBKS spectrum at psi = 0; 40 sampled cells vs the oracle
+    y, nu, L = ics.make_config(**ics.CONFIGS["zeldovich-128^3-bbks-1.5a"])
+    N = y.shape[0]
+    a = L / 128
+    s = B.Solver(y, [L] * 3, precision="fp64")
+    g = s.laguerre()
+    idx = np.random.default_rng(0).choice(N, 40, replace=False)
+    o = O.cells(y, np.zeros(N), L, "certified", idx=idx)
+    np.testing.assert_allclose(g["vol"][idx], o["vol"], rtol=0, atol=1e-10 * a ** 3)
+    assert abs(g["vol"].sum() - L ** 3) < 1e-9 * L ** 3
