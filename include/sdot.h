@@ -159,6 +159,12 @@ int sdot_displacement(sdot_ctx* ctx, double* disp);
  * binary64 without fused multiply-add. */
 int sdot_knn(sdot_ctx* ctx, int32_t* nbr);
 
+/* Per-cell status of the last evaluation (N bytes out, caller order). Bits:
+ * 1 empty, 2 capacity exceeded, 4 failed the FP32 consistency check (then
+ * re-clipped in FP64), 8 re-queued by the security test, 16 reaches a non-minimum
+ * periodic image, 32/64/128 capacity detail (polytope / face / traversal stack). */
+int sdot_cell_status(sdot_ctx* ctx, uint8_t* status);
+
 /* Number of seeds and kNN size of the context. */
 int sdot_size(const sdot_ctx* ctx, int64_t* N, int* k);
 

@@ -56,7 +56,7 @@ class sdot_stats(ctypes.Structure):
 # every symbol include/sdot.h declares
 EXPORTS = ["sdot_default_options", "sdot_create", "sdot_set_stream", "sdot_laguerre",
            "sdot_solve", "sdot_csr_copy", "sdot_get_psi", "sdot_displacement", "sdot_knn",
-           "sdot_size", "sdot_destroy", "sdot_last_error"]
+           "sdot_cell_status", "sdot_size", "sdot_destroy", "sdot_last_error"]
 
 _lib = None
 
@@ -85,6 +85,7 @@ def load(path=LIB_PATH):
     lib.sdot_get_psi.argtypes = [P, P]
     lib.sdot_displacement.argtypes = [P, P]
     lib.sdot_knn.argtypes = [P, P]
+    lib.sdot_cell_status.argtypes = [P, P]
     lib.sdot_size.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I)]
     lib.sdot_destroy.argtypes = [P]
     lib.sdot_destroy.restype = None
@@ -105,7 +106,7 @@ def _ptr(x, dtype=np.float64):
         if not x.is_contiguous():
             raise ValueError("tensor must be contiguous")
         want = {np.float64: "torch.float64", np.int32: "torch.int32",
-                np.int64: "torch.int64"}[dtype]
+                np.int64: "torch.int64", np.uint8: "torch.uint8"}[dtype]
         if str(x.dtype) != want:
             raise TypeError(f"expected {want}, got {x.dtype}")
         return ctypes.c_void_p(x.data_ptr())
@@ -174,6 +175,10 @@ def sdot_knn(ctx, nbr):
     return load().sdot_knn(ctx, _ptr(nbr, np.int32))
 
 
+def sdot_cell_status(ctx, status):
+    return load().sdot_cell_status(ctx, _ptr(status, np.uint8))
+
+
 def sdot_size(ctx):
     n = ctypes.c_int64()
     k = ctypes.c_int()
@@ -231,6 +236,11 @@ class Solver:
     def displacement(self):
         out = np.empty((self.N, 3))
         check(sdot_displacement(self.ctx, out))
+        return out
+
+    def status(self):
+        out = np.empty(self.N, dtype=np.uint8)
+        check(sdot_cell_status(self.ctx, out))
         return out
 
     def knn(self):

@@ -118,7 +118,7 @@ int eval_status(const EvalResult& r, const char* where) {
     if (r.flags & CS_CAPACITY) {
         set_error(std::string(where) + ": a cell exceeded the polytope capacity (" +
                   std::to_string(MAXP) + " planes, " + std::to_string(MAXT) + " vertices, " +
-                  std::to_string(FCAP) + " facets)");
+                  std::to_string(FCAP) + " facets); status bits " + std::to_string(r.flags));
         return SDOT_ERR_CAPACITY;
     }
     return SDOT_OK;
@@ -549,6 +549,24 @@ int sdot_displacement(sdot_ctx* c, double* disp) {
         SDOT_CUDA_TRY(cudaMemcpyAsync(disp, tgt, (size_t)d.N * 24, cudaMemcpyDeviceToHost, c->stream));
     SDOT_CUDA_TRY(cudaStreamSynchronize(c->stream));
     return SDOT_OK;
+}
+
+int sdot_cell_status(sdot_ctx* c, uint8_t* status) {
+    g_err.clear();
+    if (!c || !status) return SDOT_ERR_ARG;
+    DeviceState& d = c->d;
+    bool dev = is_device_ptr(status);
+    uint8_t* tgt = status;
+    int rc;
+    if (!dev && (rc = alloc_n(c, &tgt, d.N))) return rc;
+    rc = status_to_user(d, tgt, c->stream);
+    if (!rc && !dev &&
+        cudaMemcpyAsync(status, tgt, (size_t)d.N, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        rc = SDOT_ERR_CUDA;
+    if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = SDOT_ERR_CUDA;
+    if (!dev) dev_free(c, tgt);
+    if (rc == SDOT_ERR_CUDA) set_error("sdot_cell_status: copy failed");
+    return rc;
 }
 
 int sdot_knn(sdot_ctx* c, int32_t* nbr) {

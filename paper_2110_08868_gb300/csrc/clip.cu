@@ -184,44 +184,73 @@ __device__ __forceinline__ V3<R> vertex_of(const WarpPoly<R>& P, uint32_t t, R& 
 // drop planes no vertex references any more; returns the number of planes left
 template <typename R>
 __device__ int poly_gc(WarpPoly<R>& P, int lane) {
-    uint32_t lo = 0, hi = 0;
+    constexpr int NW = MAXP / 32;
+    uint32_t used[NW];
+#pragma unroll
+    for (int w = 0; w < NW; w++) used[w] = 0;
     for (int s = lane; s < P.nt; s += 32) {
         uint32_t t = P.tri[s];
+#pragma unroll
         for (int e = 0; e < 3; e++) {
             uint32_t q = (t >> (8 * e)) & 0xff;
-            if (q < 32) lo |= 1u << q;
-            else hi |= 1u << (q - 32);
+#pragma unroll
+            for (int w = 0; w < NW; w++)
+                if ((q >> 5) == (uint32_t)w) used[w] |= 1u << (q & 31);
         }
     }
-    lo = __reduce_or_sync(FULLMASK, lo);
-    hi = __reduce_or_sync(FULLMASK, hi);
-    lo |= 0x3fu;  // box planes keep their slots
-    int np = P.np;
-    // remap table: new slot of plane q = number of used planes below q
-    V4<R> pl0, pl1;
-    R len0 = 0, len1 = 0;
-    int32_t j0 = 0, j1 = 0;
-    bool u0 = lane < np && (lo >> lane & 1), u1 = lane + 32 < np && (hi >> lane & 1);
-    if (u0) { pl0 = P.pl[lane]; len0 = P.plen[lane]; j0 = P.pj[lane]; }
-    if (u1) { pl1 = P.pl[lane + 32]; len1 = P.plen[lane + 32]; j1 = P.pj[lane + 32]; }
-    uint32_t below = (lane == 0) ? 0u : ((1u << lane) - 1u);
-    int n0 = __popc(lo & below);
-    int n1 = __popc(lo) + __popc(hi & below);
+#pragma unroll
+    for (int w = 0; w < NW; w++) used[w] = __reduce_or_sync(FULLMASK, used[w]);
+    used[0] |= 0x3fu;  // box planes keep their slots
+    int before[NW];
+    int acc = 0;
+#pragma unroll
+    for (int w = 0; w < NW; w++) {
+        before[w] = acc;
+        acc += __popc(used[w]);
+    }
+    const int nn = acc;
+    const int np = P.np;
+    const uint32_t below = (lane == 0) ? 0u : ((1u << lane) - 1u);
+    // move the surviving planes down (read all, then write)
+    V4<R> pl[NW];
+    R len[NW];
+    int32_t pj[NW];
+    int dst[NW];
+#pragma unroll
+    for (int w = 0; w < NW; w++) {
+        int q = lane + 32 * w;
+        dst[w] = -1;
+        if (q < np && (used[w] >> lane & 1u)) {
+            pl[w] = P.pl[q];
+            len[w] = P.plen[q];
+            pj[w] = P.pj[q];
+            dst[w] = before[w] + __popc(used[w] & below);
+        }
+    }
     __syncwarp();
-    if (u0) { P.pl[n0] = pl0; P.plen[n0] = len0; P.pj[n0] = j0; }
-    if (u1) { P.pl[n1] = pl1; P.plen[n1] = len1; P.pj[n1] = j1; }
+#pragma unroll
+    for (int w = 0; w < NW; w++)
+        if (dst[w] >= 0) {
+            P.pl[dst[w]] = pl[w];
+            P.plen[dst[w]] = len[w];
+            P.pj[dst[w]] = pj[w];
+        }
     __syncwarp();
     for (int s = lane; s < P.nt; s += 32) {
         uint32_t t = P.tri[s], r = 0;
+#pragma unroll
         for (int e = 0; e < 3; e++) {
             uint32_t q = (t >> (8 * e)) & 0xff;
-            uint32_t nq = q < 32 ? __popc(lo & ((q == 0) ? 0u : ((1u << q) - 1u)))
-                                 : __popc(lo) + __popc(hi & (((q - 32) == 0) ? 0u : ((1u << (q - 32)) - 1u)));
+            uint32_t w = q >> 5, b = q & 31;
+            uint32_t m = (b == 0) ? 0u : ((1u << b) - 1u);
+            uint32_t nq = 0;
+#pragma unroll
+            for (int u = 0; u < NW; u++)
+                if ((uint32_t)u == w) nq = before[u] + __popc(used[u] & m);
             r |= nq << (8 * e);
         }
         P.tri[s] = r;
     }
-    int nn = __popc(lo) + __popc(hi);
     __syncwarp();
     if (lane == 0) P.np = nn;
     __syncwarp();
@@ -500,7 +529,7 @@ __device__ bool traverse(WarpPoly<R>& P, const ClipParams& cp, int64_t i, const 
             if (cl > 0) {
                 int n = __popc(sm);
                 if (sp + n > STACK) {
-                    st |= CS_CAPACITY;
+                    st |= CS_CAPACITY | CS_CAP_STACK;
                     return false;
                 }
                 uint32_t below = (lane == 0) ? 0u : ((1u << lane) - 1u);
@@ -536,8 +565,10 @@ __device__ bool traverse(WarpPoly<R>& P, const ClipParams& cp, int64_t i, const 
                         int oj = (int)yj.w;
                         if (d2 < d2k || (d2 == d2k && oj <= ok_k)) continue;
                         // already a plane of the polytope?
-                        bool dup = (lane < P.np && P.pj[lane] == j) ||
-                                   (lane + 32 < P.np && P.pj[lane + 32] == j);
+                        bool dup = false;
+#pragma unroll
+                        for (int w = 0; w < MAXP / 32; w++)
+                            dup |= (lane + 32 * w < P.np && P.pj[lane + 32 * w] == j);
                         if (__any_sync(FULLMASK, dup)) continue;
                         double nxd, nyd, nzd, wd;
                         make_plane(cp, yi, psii, j, nxd, nyd, nzd, wd);
@@ -565,7 +596,7 @@ __device__ bool traverse(WarpPoly<R>& P, const ClipParams& cp, int64_t i, const 
                                 return false;
                             }
                             if (rc == CLIP_CAP) {
-                                st |= CS_CAPACITY;
+                                st |= CS_CAPACITY | CS_CAP_POLY;
                                 return false;
                             }
                             if (rc == CLIP_CUT) Rz = (float)poly_radius(P, zr, lane) * 1.0001f + 1e-6f;
@@ -583,9 +614,10 @@ template <typename R>
 __device__ void integrate(WarpPoly<R>& P, const ClipParams& cp, int64_t i, int lane,
                           bool& bad, uint32_t& st) {
     double vol6 = 0, mx = 0, my = 0, mz = 0, sx = 0, sy = 0, sz = 0, sabs = 0;
+    constexpr int FPL = MAXP / 32;  // faces handled per lane
     int nf = 0;
-    int32_t fj[2];
-    double fc[2];
+    int32_t fj[FPL];
+    double fc[FPL];
     const int nt = P.nt;
     for (int f = lane; f < ((P.np + 31) / 32) * 32; f += 32) {
         // faces f are handled in rounds so every lane runs the same triangle loop
@@ -606,7 +638,7 @@ __device__ void integrate(WarpPoly<R>& P, const ClipParams& cp, int64_t i, int l
         }
         if (!active || m == 0) continue;
         if (m > MAXFV) {
-            st |= CS_CAPACITY;
+            st |= CS_CAPACITY | CS_CAP_FACE;
             continue;
         }
         if (m < 3) {
@@ -657,7 +689,7 @@ __device__ void integrate(WarpPoly<R>& P, const ClipParams& cp, int64_t i, int l
         sabs += A;
         int32_t j = P.pj[f];
         if (j >= 0 && A > 0.0) {
-            if (nf < 2) {
+            if (nf < FPL) {
                 fj[nf] = j;
                 fc[nf] = A * cp.a / (double)P.plen[f];
             }
@@ -679,10 +711,10 @@ __device__ void integrate(WarpPoly<R>& P, const ClipParams& cp, int64_t i, int l
         if (lane >= o) incl += y;
     }
     int total = __shfl_sync(FULLMASK, incl, 31);
-    if (total > FCAP) st |= CS_CAPACITY;
+    if (total > FCAP) st |= CS_CAPACITY | CS_CAP_FACE;
     else {
         int pos = incl - nf;
-        for (int q = 0; q < nf && q < 2; q++) {
+        for (int q = 0; q < nf && q < FPL; q++) {
             cp.fcol[i * FCAP + pos + q] = fj[q];
             cp.fval[i * FCAP + pos + q] = fc[q];
         }
@@ -715,7 +747,8 @@ __device__ void integrate(WarpPoly<R>& P, const ClipParams& cp, int64_t i, int l
 template <typename R, int MODE>
 __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
     clip_kernel(ClipParams cp) {
-    __shared__ WarpPoly<R> polys[WARPS_PER_BLOCK];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    WarpPoly<R>* polys = reinterpret_cast<WarpPoly<R>*>(smem_raw);
     const int lane = threadIdx.x & 31;
     WarpPoly<R>& P = polys[threadIdx.x >> 5];
     // global upper bound of psi (top pyramid level)
@@ -759,7 +792,7 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
                 R plen = sqrt(pn.x * pn.x + pn.y * pn.y + pn.z * pn.z);
                 int rc = poly_clip(P, pn, plen, ju, lane, bad);
                 if (rc == CLIP_EMPTY) { emptied = 1; break; }
-                if (rc == CLIP_CAP) { st |= CS_CAPACITY; break; }
+                if (rc == CLIP_CAP) { st |= CS_CAPACITY | CS_CAP_POLY; break; }
             }
             if (emptied || (st & CS_CAPACITY)) break;
         }
@@ -952,17 +985,20 @@ __global__ void cell_reduce_final(const double* __restrict__ part, int nb, doubl
 template <typename R, int MODE>
 static int launch_clip(const ClipParams& cp, cudaStream_t s) {
     static int blocks = 0;
+    const size_t smem = sizeof(WarpPoly<R>) * WARPS_PER_BLOCK;
     if (blocks == 0) {
+        SDOT_CUDA_TRY(cudaFuncSetAttribute(clip_kernel<R, MODE>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, clip_kernel<R, MODE>,
-                                                      WARPS_PER_BLOCK * 32, 0);
+                                                      WARPS_PER_BLOCK * 32, smem);
         if (per_sm < 1) per_sm = 1;
         blocks = per_sm * num_sms();
     }
     int64_t need = (cp.nwork + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
     int nb = (int)(need < blocks ? need : blocks);
     if (nb < 1) return SDOT_OK;
-    clip_kernel<R, MODE><<<nb, WARPS_PER_BLOCK * 32, 0, s>>>(cp);
+    clip_kernel<R, MODE><<<nb, WARPS_PER_BLOCK * 32, smem, s>>>(cp);
     SDOT_CUDA_TRY(cudaGetLastError());
     return SDOT_OK;
 }

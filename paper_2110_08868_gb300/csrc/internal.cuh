@@ -28,9 +28,9 @@ struct __align__(32) Pos4 {
 // capacities
 // ---------------------------------------------------------------------------
 constexpr int KMAX = 64;        // largest kNN size
-constexpr int MAXP = 64;        // planes per polytope (6 box planes included)
-constexpr int MAXT = 128;       // vertices (dual triangles) per polytope
-constexpr int FCAP = 48;        // facets stored per cell for the Hessian
+constexpr int MAXP = 96;        // planes per polytope (6 box planes included)
+constexpr int MAXT = 192;       // vertices (dual triangles) per polytope
+constexpr int FCAP = 64;        // facets stored per cell for the Hessian
 constexpr int MAXFV = 32;       // vertices per face during integration
 constexpr int STACK = 256;      // traversal stack entries per warp
 constexpr int MAXLEV = 8;       // pyramid levels
@@ -44,6 +44,9 @@ enum : uint32_t {
     CS_INCONSISTENT = 4,   // FP32 consistency check failed
     CS_UNCERTIFIED = 8,    // security test found a possible unseen cutter
     CS_TOO_LARGE = 16,     // cell reaches a non-minimum periodic image
+    CS_CAP_POLY = 32,      // detail of CS_CAPACITY: planes or vertices
+    CS_CAP_FACE = 64,      // detail of CS_CAPACITY: facets or vertices of one face
+    CS_CAP_STACK = 128,    // detail of CS_CAPACITY: traversal stack
 };
 
 // ---------------------------------------------------------------------------
@@ -165,6 +168,7 @@ int scatter_to_user(const DeviceState& d, const double* sorted, double* user, in
 int gather_from_user(const DeviceState& d, const double* user, double* sorted, int width,
                      cudaStream_t s);
 int centroids_user(const DeviceState& d, double* out_user, int wrap_abs, cudaStream_t s);
+int status_to_user(const DeviceState& d, uint8_t* out_user, cudaStream_t s);
 int check_masses(const DeviceState& d, double* sum_out, double* min_out, cudaStream_t s);
 
 }  // namespace sdot

@@ -442,6 +442,18 @@ __global__ void centroid_kernel(const Pos4* __restrict__ pos, const double* __re
     }
 }
 
+__global__ void status_kernel(const uint8_t* __restrict__ st, const int32_t* __restrict__ perm,
+                              int64_t N, uint8_t* __restrict__ out) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < N) out[perm[s]] = st[s];
+}
+
+int status_to_user(const DeviceState& d, uint8_t* out, cudaStream_t s) {
+    status_kernel<<<(unsigned)((d.N + 255) / 256), 256, 0, s>>>(d.status, d.perm, d.N, out);
+    SDOT_CUDA_TRY(cudaGetLastError());
+    return SDOT_OK;
+}
+
 int centroids_user(const DeviceState& d, double* out, int wrap_abs, cudaStream_t s) {
     centroid_kernel<<<(unsigned)((d.N + 255) / 256), 256, 0, s>>>(
         d.pos, d.m1, d.vol, d.perm, d.N, d.L[0], d.L[1], d.L[2], wrap_abs, out);
