@@ -52,7 +52,7 @@ def build(verbose=False, force=False, extra=()):
             jobs.append([nvcc()] + _flags(extra) + ["-c", s, "-o", o])
 
     def run(cmd):
-        r = subprocess.run(cmd, capture_output=True, text=True)
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=900)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed:\n" + " ".join(cmd) + "\n" + r.stdout + r.stderr)
         if verbose and (r.stdout or r.stderr):

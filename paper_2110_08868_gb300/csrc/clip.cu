@@ -54,6 +54,7 @@ struct WarpPoly {
     V3<R> v[MAXT];          // vertex positions
     uint32_t scratch[MAXT]; // removed vertices during a clip
     uint32_t fresh[MAXT];   // new vertices during a clip
+    V3<R> freshv[MAXT];     // their positions
     uint32_t stack[STACK];  // traversal stack: level << 27 | node
     int np, nt;
 };
@@ -183,7 +184,7 @@ __device__ __forceinline__ V3<R> vertex_of(const WarpPoly<R>& P, uint32_t t, R& 
 
 // drop planes no vertex references any more; returns the number of planes left
 template <typename R>
-__device__ int poly_gc(WarpPoly<R>& P, int lane) {
+__device__ __noinline__ int poly_gc(WarpPoly<R>& P, int lane) {
     constexpr int NW = MAXP / 32;
     uint32_t used[NW];
 #pragma unroll
@@ -259,21 +260,36 @@ __device__ int poly_gc(WarpPoly<R>& P, int lane) {
 
 enum { CLIP_NONE = 0, CLIP_CUT = 1, CLIP_EMPTY = 2, CLIP_CAP = 3 };
 
-// Clip by p.n <= w (tag j). FP32 conditioning problems set *bad.
+// relative tolerance of the vertex classification: a vertex counts as outside only
+// when it is beyond the plane by more than this fraction of the terms involved, so
+// planes that merely touch an edge or a corner (lattice-like degeneracy) do not cut
 template <typename R>
-__device__ int poly_clip(WarpPoly<R>& P, const V4<R>& pn, R plen, int32_t j, int lane,
+__device__ __forceinline__ R class_eps() {
+    return sizeof(R) == 4 ? R(1e-6) : R(1e-13);
+}
+template <typename R>
+__device__ __forceinline__ bool beyond(const V3<R>& v, const V4<R>& pn, R plen, R& sd) {
+    sd = v.x * pn.x + v.y * pn.y + v.z * pn.z - pn.w;
+    R scale = fabs(pn.w) + plen * (fabs(v.x) + fabs(v.y) + fabs(v.z));
+    return sd > class_eps<R>() * scale;
+}
+
+// Clip by p.n <= w (tag j). Non-finite geometry sets bad.
+template <typename R>
+__device__ __noinline__ int poly_clip(WarpPoly<R>& P, const V4<R>& pn, R plen, int32_t j, int lane,
                          bool& bad) {
+    constexpr int SL = MAXT / 32;  // vertex slots per lane
     const int nt = P.nt;
-    bool out[MAXT / 32];
-    uint32_t m[MAXT / 32];
+    bool out[SL];
+    uint32_t m[SL];
     int nrem = 0;
 #pragma unroll
-    for (int t = 0; t < MAXT / 32; t++) {
+    for (int t = 0; t < SL; t++) {
         int s = lane + 32 * t;
         out[t] = false;
         if (s < nt) {
-            V3<R> v = P.v[s];
-            out[t] = v.x * pn.x + v.y * pn.y + v.z * pn.z - pn.w > R(0);
+            R sd;
+            out[t] = beyond(P.v[s], pn, plen, sd);
         }
         m[t] = __ballot_sync(FULLMASK, out[t]);
         nrem += __popc(m[t]);
@@ -285,25 +301,31 @@ __device__ int poly_clip(WarpPoly<R>& P, const V4<R>& pn, R plen, int32_t j, int
     }
     const uint32_t ps = (uint32_t)P.np;
     const uint32_t below = (lane == 0) ? 0u : ((1u << lane) - 1u);
-    // removed list
+    // removed list: triangle | slot << 24
     {
         int base = 0;
 #pragma unroll
-        for (int t = 0; t < MAXT / 32; t++) {
-            if (out[t]) P.scratch[base + __popc(m[t] & below)] = P.tri[lane + 32 * t];
+        for (int t = 0; t < SL; t++) {
+            if (out[t]) P.scratch[base + __popc(m[t] & below)] =
+                P.tri[lane + 32 * t] | ((uint32_t)(lane + 32 * t) << 24);
             base += __popc(m[t]);
         }
     }
+    if (lane == 0) {
+        P.pl[ps] = pn;
+        P.plen[ps] = plen;
+        P.pj[ps] = j;
+    }
     __syncwarp();
-    // boundary edges of the removed region
+    // boundary edges of the removed region: dual edges whose reverse is not removed
     uint32_t bmask = 0;  // 3 bits per removed entry handled by this lane
     int cnt = 0;
     for (int r = lane, e = 0; r < nrem; r += 32, e++) {
-        uint32_t t = P.scratch[r];
+        uint32_t t = P.scratch[r] & 0xffffffu;
         uint32_t a = t & 0xff, b = (t >> 8) & 0xff, c = (t >> 16) & 0xff;
         bool fab = false, fbc = false, fca = false;
         for (int q = 0; q < nrem; q++) {
-            uint32_t u = P.scratch[q];
+            uint32_t u = P.scratch[q] & 0xffffffu;
             fab |= has_edge(u, b, a);
             fbc |= has_edge(u, c, b);
             fca |= has_edge(u, a, c);
@@ -312,7 +334,6 @@ __device__ int poly_clip(WarpPoly<R>& P, const V4<R>& pn, R plen, int32_t j, int
         bmask |= bits << (3 * e);
         cnt += __popc(bits);
     }
-    // warp exclusive scan of cnt
     int incl = cnt;
     for (int o = 1; o < 32; o <<= 1) {
         int y = __shfl_up_sync(FULLMASK, incl, o);
@@ -321,29 +342,66 @@ __device__ int poly_clip(WarpPoly<R>& P, const V4<R>& pn, R plen, int32_t j, int
     const int nnew = __shfl_sync(FULLMASK, incl, 31);
     const int nkept = nt - nrem;
     if (nkept + nnew > MAXT) return CLIP_CAP;
+    // new vertices: the plane through the edge's two planes and the new plane; when
+    // that system is ill-conditioned (the new plane almost parallel to the edge) the
+    // vertex is interpolated on the edge between its kept and removed end points
+    bool lbad = false;
     {
         int pos = incl - cnt;
+        const R dtol = sizeof(R) == 4 ? R(1e-3) : R(1e-6);
         for (int r = lane, e = 0; r < nrem; r += 32, e++) {
-            uint32_t t = P.scratch[r];
-            uint32_t a = t & 0xff, b = (t >> 8) & 0xff, c = (t >> 16) & 0xff;
+            uint32_t rr = P.scratch[r];
+            uint32_t t = rr & 0xffffffu, sr = rr >> 24;
+            uint32_t tv[3] = {t & 0xff, (t >> 8) & 0xff, (t >> 16) & 0xff};
             uint32_t bits = (bmask >> (3 * e)) & 7u;
-            if (bits & 1u) P.fresh[pos++] = pack3(a, b, ps);
-            if (bits & 2u) P.fresh[pos++] = pack3(b, c, ps);
-            if (bits & 4u) P.fresh[pos++] = pack3(c, a, ps);
+            for (int k = 0; k < 3; k++) {
+                if (!(bits >> k & 1u)) continue;
+                uint32_t x = tv[k], y = tv[(k + 1) % 3];
+                uint32_t nt3 = pack3(x, y, ps);
+                R det_rel;
+                V3<R> v = vertex_of(P, nt3, det_rel);
+                if (!(det_rel > dtol)) {
+                    int sk = -1;
+                    for (int q = 0; q < nt; q++) {
+                        bool o = (m[q >> 5] >> (q & 31)) & 1u;
+                        if (!o && has_edge(P.tri[q], y, x)) { sk = q; break; }
+                    }
+                    if (sk >= 0) {
+                        V3<R> vk = P.v[sk], vr = P.v[sr];
+                        R s_k, s_r;
+                        beyond(vk, pn, plen, s_k);
+                        beyond(vr, pn, plen, s_r);
+                        R tt = R(0);
+                        if (s_k < R(0) && s_r > s_k) tt = s_k / (s_k - s_r);
+                        tt = tt < R(0) ? R(0) : (tt > R(1) ? R(1) : tt);
+                        v.x = vk.x + tt * (vr.x - vk.x);
+                        v.y = vk.y + tt * (vr.y - vk.y);
+                        v.z = vk.z + tt * (vr.z - vk.z);
+                    } else {
+                        lbad = true;
+                    }
+                }
+                if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z))) lbad = true;
+                P.fresh[pos] = nt3;
+                P.freshv[pos] = v;
+                pos++;
+            }
         }
     }
-    // compact the kept vertices
+    __syncwarp();
+    // compact the kept vertices (read all, then write)
     {
-        uint32_t kt[MAXT / 32];
-        V3<R> kv[MAXT / 32];
-        int dst[MAXT / 32];
+        uint32_t kt[SL];
+        V3<R> kv[SL];
+        int dst[SL];
         int base = 0;
 #pragma unroll
-        for (int t = 0; t < MAXT / 32; t++) {
+        for (int t = 0; t < SL; t++) {
             int s = lane + 32 * t;
-            uint32_t km = __ballot_sync(FULLMASK, s < nt && !out[t]);
+            bool keep = s < nt && !out[t];
+            uint32_t km = __ballot_sync(FULLMASK, keep);
             dst[t] = -1;
-            if (s < nt && !out[t]) {
+            if (keep) {
                 kt[t] = P.tri[s];
                 kv[t] = P.v[s];
                 dst[t] = base + __popc(km & below);
@@ -352,28 +410,20 @@ __device__ int poly_clip(WarpPoly<R>& P, const V4<R>& pn, R plen, int32_t j, int
         }
         __syncwarp();
 #pragma unroll
-        for (int t = 0; t < MAXT / 32; t++)
+        for (int t = 0; t < SL; t++)
             if (dst[t] >= 0) {
                 P.tri[dst[t]] = kt[t];
                 P.v[dst[t]] = kv[t];
             }
     }
+    __syncwarp();
+    for (int n = lane; n < nnew; n += 32) {
+        P.tri[nkept + n] = P.fresh[n];
+        P.v[nkept + n] = P.freshv[n];
+    }
     if (lane == 0) {
-        P.pl[ps] = pn;
-        P.plen[ps] = plen;
-        P.pj[ps] = j;
         P.np = ps + 1;
         P.nt = nkept + nnew;
-    }
-    __syncwarp();
-    bool lbad = false;
-    for (int n = lane; n < nnew; n += 32) {
-        uint32_t t = P.fresh[n];
-        R det_rel;
-        V3<R> v = vertex_of(P, t, det_rel);
-        if (!(det_rel > R(sizeof(R) == 4 ? 1e-6 : 1e-14))) lbad = true;
-        P.tri[nkept + n] = t;
-        P.v[nkept + n] = v;
     }
     if (__any_sync(FULLMASK, lbad)) bad = true;
     __syncwarp();
@@ -472,6 +522,107 @@ __device__ __forceinline__ bool seed_may_cut(const ClipParams& cp, const Anchor&
 }
 
 enum { MODE_CERTIFY = 0, MODE_FULL = 1 };
+enum { LEAF_OK = 0, LEAF_STOP = 1 };
+
+// Test every seed of one grid cell against the polytope. MODE_CERTIFY: stop at the
+// first unseen seed whose plane cuts. MODE_FULL: clip by every such seed.
+template <typename R, int MODE>
+__device__ __noinline__ int process_leaf(WarpPoly<R>& P, const ClipParams& cp, int64_t i, const Pos4& yi,
+                            double psii, const Anchor& an, float& Rz, const V3<R>& zr,
+                            double d2k, int ok_k, int lane, bool& bad, uint32_t& st,
+                            int64_t leaf) {
+    int32_t sb = cp.cell_start[leaf], se = cp.cell_start[leaf + 1];
+    for (int32_t s0 = sb; s0 < se; s0 += 32) {
+        int32_t s = s0 + lane;
+        bool cand = false;
+        if (s < se && s != (int32_t)i) cand = seed_may_cut(cp, an, Rz, cp.posf[s]);
+        uint32_t cm = __ballot_sync(FULLMASK, cand);
+        while (cm) {
+            int c = __ffs(cm) - 1;
+            cm &= cm - 1;
+            int32_t j = s0 + c;
+            // seen in the kNN list?
+            Pos4 yj = cp.pos[j];
+            double d2 = exact_d2(yi, yj, cp);
+            int oj = (int)yj.w;
+            if (d2 < d2k || (d2 == d2k && oj <= ok_k)) continue;
+            // already a plane of the polytope?
+            bool dup = false;
+#pragma unroll
+            for (int w = 0; w < MAXP / 32; w++)
+                dup |= (lane + 32 * w < P.np && P.pj[lane + 32 * w] == j);
+            if (__any_sync(FULLMASK, dup)) continue;
+            double nxd, nyd, nzd, wd;
+            make_plane(cp, yi, psii, j, nxd, nyd, nzd, wd);
+            V4<R> pn;
+            pn.x = (R)nxd;
+            pn.y = (R)nyd;
+            pn.z = (R)nzd;
+            pn.w = (R)wd;
+            R plen = (R)sqrt(nxd * nxd + nyd * nyd + nzd * nzd);
+            if (MODE == MODE_CERTIFY) {
+                bool o = false;
+                for (int q = lane; q < P.nt; q += 32) {
+                    R sd;
+                    o |= beyond(P.v[q], pn, plen, sd);
+                }
+                if (__any_sync(FULLMASK, o)) {
+                    st |= CS_UNCERTIFIED;
+                    return LEAF_STOP;
+                }
+            } else {
+                int rc = poly_clip(P, pn, plen, j, lane, bad);
+                if (rc == CLIP_EMPTY) {
+                    st |= CS_EMPTY;
+                    return LEAF_STOP;
+                }
+                if (rc == CLIP_CAP) {
+                    st |= CS_CAPACITY | CS_CAP_POLY;
+                    return LEAF_STOP;
+                }
+                if (rc == CLIP_CUT) Rz = (float)poly_radius(P, zr, lane) * 1.0001f + 1e-6f;
+            }
+        }
+    }
+    return LEAF_OK;
+}
+
+// Near-first pass for re-queued cells: clip by the seeds of the grid cells in
+// Chebyshev rings around the anchor's grid cell, so the polytope is small before the
+// pyramid walk (which visits nodes in no particular order) starts.
+template <typename R>
+__device__ __noinline__ bool ring_walk(WarpPoly<R>& P, const ClipParams& cp, int64_t i, const Pos4& yi,
+                          double psii, const Anchor& an, const V3<R>& zr, double d2k, int ok_k,
+                          int lane, bool& bad, uint32_t& st) {
+    int ca[3];
+    float hmin = 1e30f;
+    for (int a = 0; a < 3; a++) {
+        int c = (int)floorf(an.zabs[a] / cp.ht[a]);
+        ca[a] = c < 0 ? 0 : (c >= cp.G[a] ? cp.G[a] - 1 : c);
+        hmin = fminf(hmin, cp.ht[a]);
+    }
+    const int Gmin = min(cp.G[0], min(cp.G[1], cp.G[2]));
+    float Rz = (float)poly_radius(P, zr, lane) * 1.0001f + 1e-6f;
+    for (int r = 0; r <= 3; r++) {
+        if (2 * r + 1 > Gmin) break;
+        if (r >= 2 && (float)(r - 1) * hmin > 2.f * Rz) break;
+        for (int oz = -r; oz <= r; oz++)
+            for (int oy = -r; oy <= r; oy++) {
+                bool face = (oz == -r || oz == r || oy == -r || oy == r);
+                int step = (face || r == 0) ? 1 : 2 * r;
+                for (int ox = -r; ox <= r; ox += step) {
+                    int cx = ((ca[0] + ox) % cp.G[0] + cp.G[0]) % cp.G[0];
+                    int cy = ((ca[1] + oy) % cp.G[1] + cp.G[1]) % cp.G[1];
+                    int cz = ((ca[2] + oz) % cp.G[2] + cp.G[2]) % cp.G[2];
+                    int64_t leaf = ((int64_t)cz * cp.G[1] + cy) * cp.G[0] + cx;
+                    if (process_leaf<R, MODE_FULL>(P, cp, i, yi, psii, an, Rz, zr, d2k, ok_k, lane,
+                                                   bad, st, leaf) == LEAF_STOP)
+                        return false;
+                }
+            }
+    }
+    return true;
+}
 
 // Walk the pyramid. MODE_CERTIFY: return false as soon as an unseen seed cuts the
 // polytope. MODE_FULL: clip every such seed. Returns true when the walk completed.
@@ -483,6 +634,9 @@ __device__ bool traverse(WarpPoly<R>& P, const ClipParams& cp, int64_t i, const 
     zr.x = (R)an.z[0];
     zr.y = (R)an.z[1];
     zr.z = (R)an.z[2];
+    if (MODE == MODE_FULL) {
+        if (!ring_walk(P, cp, i, yi, psii, an, zr, d2k, ok_k, lane, bad, st)) return false;
+    }
     float Rz = (float)poly_radius(P, zr, lane) * 1.0001f + 1e-6f;
     const int top = cp.pyr.nlev;  // virtual root level
     int sp = 0;
@@ -549,60 +703,9 @@ __device__ bool traverse(WarpPoly<R>& P, const ClipParams& cp, int64_t i, const 
                 int ly = __shfl_sync(FULLMASK, cy, src);
                 int lz = __shfl_sync(FULLMASK, cz, src);
                 int64_t leaf = ((int64_t)lz * cp.G[1] + ly) * cp.G[0] + lx;
-                int32_t sb = cp.cell_start[leaf], se = cp.cell_start[leaf + 1];
-                for (int32_t s0 = sb; s0 < se; s0 += 32) {
-                    int32_t s = s0 + lane;
-                    bool cand = false;
-                    if (s < se && s != (int32_t)i) cand = seed_may_cut(cp, an, Rz, cp.posf[s]);
-                    uint32_t cm = __ballot_sync(FULLMASK, cand);
-                    while (cm) {
-                        int cl2 = __ffs(cm) - 1;
-                        cm &= cm - 1;
-                        int32_t j = s0 + cl2;
-                        // seen in the kNN list?
-                        Pos4 yj = cp.pos[j];
-                        double d2 = exact_d2(yi, yj, cp);
-                        int oj = (int)yj.w;
-                        if (d2 < d2k || (d2 == d2k && oj <= ok_k)) continue;
-                        // already a plane of the polytope?
-                        bool dup = false;
-#pragma unroll
-                        for (int w = 0; w < MAXP / 32; w++)
-                            dup |= (lane + 32 * w < P.np && P.pj[lane + 32 * w] == j);
-                        if (__any_sync(FULLMASK, dup)) continue;
-                        double nxd, nyd, nzd, wd;
-                        make_plane(cp, yi, psii, j, nxd, nyd, nzd, wd);
-                        V4<R> pn;
-                        pn.x = (R)nxd;
-                        pn.y = (R)nyd;
-                        pn.z = (R)nzd;
-                        pn.w = (R)wd;
-                        R plen = (R)sqrt(nxd * nxd + nyd * nyd + nzd * nzd);
-                        if (MODE == MODE_CERTIFY) {
-                            // does it actually cut? (classification only)
-                            bool o = false;
-                            for (int q = lane; q < P.nt; q += 32) {
-                                V3<R> v = P.v[q];
-                                o |= v.x * pn.x + v.y * pn.y + v.z * pn.z - pn.w > R(0);
-                            }
-                            if (__any_sync(FULLMASK, o)) {
-                                st |= CS_UNCERTIFIED;
-                                return false;
-                            }
-                        } else {
-                            int rc = poly_clip(P, pn, plen, j, lane, bad);
-                            if (rc == CLIP_EMPTY) {
-                                st |= CS_EMPTY;
-                                return false;
-                            }
-                            if (rc == CLIP_CAP) {
-                                st |= CS_CAPACITY | CS_CAP_POLY;
-                                return false;
-                            }
-                            if (rc == CLIP_CUT) Rz = (float)poly_radius(P, zr, lane) * 1.0001f + 1e-6f;
-                        }
-                    }
-                }
+                if (process_leaf<R, MODE>(P, cp, i, yi, psii, an, Rz, zr, d2k, ok_k, lane, bad, st,
+                                          leaf) == LEAF_STOP)
+                    return false;
             }
         }
     }
@@ -611,7 +714,7 @@ __device__ bool traverse(WarpPoly<R>& P, const ClipParams& cp, int64_t i, const 
 
 // Integrate the polytope and write the outputs of cell i.
 template <typename R>
-__device__ void integrate(WarpPoly<R>& P, const ClipParams& cp, int64_t i, int lane,
+__device__ __noinline__ void integrate(WarpPoly<R>& P, const ClipParams& cp, int64_t i, int lane,
                           bool& bad, uint32_t& st) {
     double vol6 = 0, mx = 0, my = 0, mz = 0, sx = 0, sy = 0, sz = 0, sabs = 0;
     constexpr int FPL = MAXP / 32;  // faces handled per lane
