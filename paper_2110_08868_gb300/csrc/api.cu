@@ -156,9 +156,12 @@ void log_iter(const sdot_ctx* c, int it, const EvalResult& r, double alpha, int 
     fprintf(stderr,
             "{\"newton_it\": %d, \"max_rel_err\": %.6e, \"l2_err\": %.6e, \"min_vol\": %.6e, "
             "\"alpha\": %g, \"cg_iters\": %d, \"cg_rel_res\": %.3e, \"trials\": %d, "
-            "\"requeued\": %lld, \"reclipped_fp64\": %lld, \"clip_ms\": %.3f}\n",
+            "\"requeued\": %lld, \"reclipped_fp64\": %lld, \"clip_ms\": %.3f, "
+            "\"pass_ms\": [%.3f, %.3f, %.3f], \"work\": [%llu, %llu, %llu, %llu, %llu, %llu, %llu, %llu]}\n",
             it, r.max_rel_err, r.l2_err, r.min_vol, alpha, cg_it, cg_res, trials,
-            (long long)r.requeued, (long long)r.reclipped, r.ms);
+            (long long)r.requeued, (long long)r.reclipped, r.ms, r.ms_pass[0], r.ms_pass[1],
+            r.ms_pass[2], r.work[0], r.work[1], r.work[2], r.work[3], r.work[4], r.work[5],
+            r.work[6], r.work[7]);
 }
 
 }  // namespace
@@ -262,7 +265,7 @@ int sdot_create(const double* pos, const double* mass, int64_t N, const double b
         (rc = alloc_n(c, &d.status, N)) || (rc = alloc_n(c, &d.fcnt, N)) ||
         (rc = alloc_n(c, &d.fcol, N * FCAP)) || (rc = alloc_n(c, &d.fval, N * FCAP)) ||
         (rc = alloc_n(c, &d.queue, N)) || (rc = alloc_n(c, &d.queue64, N)) ||
-        (rc = alloc_n(c, &d.counters, 16)) || (rc = alloc_n(c, &d.row_ptr, N + 1)) ||
+        (rc = alloc_n(c, &d.counters, 32)) || (rc = alloc_n(c, &d.row_ptr, N + 1)) ||
         (rc = alloc_n(c, &d.rowcnt, N + 1)) || (rc = alloc_n(c, &d.x, N)) ||
         (rc = alloc_n(c, &d.r, N)) || (rc = alloc_n(c, &d.z, N)) || (rc = alloc_n(c, &d.p, N)) ||
         (rc = alloc_n(c, &d.q, N)) || (rc = alloc_n(c, &d.dinv, N)) ||

@@ -57,7 +57,22 @@ struct WarpPoly {
     V3<R> freshv[MAXT];     // their positions
     uint32_t stack[STACK];  // traversal stack: level << 27 | node
     int np, nt;
+    uint32_t wc[8];         // work counters of the current cell (diagnostic builds)
 };
+
+// Work counters, compiled in only with -DSDOT_COUNTERS (diagnostic builds):
+// 0 clip calls, 1 cuts, 2 node tests, 3 leaf visits, 4 seed tests, 5 candidates,
+// 6 cells, 7 pyramid-walk rounds
+#ifdef SDOT_COUNTERS
+#define WCOUNT(P, k, n)                 \
+    do {                                \
+        if ((threadIdx.x & 31) == 0) (P).wc[k] += (n); \
+    } while (0)
+#else
+#define WCOUNT(P, k, n) \
+    do {                \
+    } while (0)
+#endif
 
 struct ClipParams {
     int64_t N;
@@ -89,6 +104,7 @@ struct ClipParams {
     int32_t* work_counter;
     const int32_t* worklist;  // null: cells 0..nwork-1
     int64_t nwork;
+    unsigned long long* counters64;  // diagnostic work counters (8)
 };
 
 __device__ __forceinline__ double wrapd(double dx, double L, double halfL) {
@@ -294,7 +310,9 @@ __device__ __noinline__ int poly_clip(WarpPoly<R>& P, const V4<R>& pn, R plen, i
         m[t] = __ballot_sync(FULLMASK, out[t]);
         nrem += __popc(m[t]);
     }
+    WCOUNT(P, 0, 1);
     if (nrem == 0) return CLIP_NONE;
+    WCOUNT(P, 1, 1);
     if (nrem == nt) return CLIP_EMPTY;
     if (P.np >= MAXP) {
         if (poly_gc(P, lane) >= MAXP) return CLIP_CAP;
@@ -532,11 +550,14 @@ __device__ __noinline__ int process_leaf(WarpPoly<R>& P, const ClipParams& cp, i
                             double d2k, int ok_k, int lane, bool& bad, uint32_t& st,
                             int64_t leaf) {
     int32_t sb = cp.cell_start[leaf], se = cp.cell_start[leaf + 1];
+    WCOUNT(P, 3, 1);
+    WCOUNT(P, 4, se - sb);
     for (int32_t s0 = sb; s0 < se; s0 += 32) {
         int32_t s = s0 + lane;
         bool cand = false;
         if (s < se && s != (int32_t)i) cand = seed_may_cut(cp, an, Rz, cp.posf[s]);
         uint32_t cm = __ballot_sync(FULLMASK, cand);
+        WCOUNT(P, 5, __popc(cm));
         while (cm) {
             int c = __ffs(cm) - 1;
             cm &= cm - 1;
@@ -668,6 +689,8 @@ __device__ bool traverse(WarpPoly<R>& P, const ClipParams& cp, int64_t i, const 
             nz = min(4, cdz - z0);
         }
         const int nch = nx * ny * nz;  // <= 64
+        WCOUNT(P, 2, nch);
+        WCOUNT(P, 7, 1);
         for (int base = 0; base < nch; base += 32) {
             int t = base + lane;
             bool surv = false;
@@ -873,6 +896,11 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
         const double psii = cp.psi[i];
         bool bad = false;
         uint32_t st = 0;
+#ifdef SDOT_COUNTERS
+        if (lane < 8) P.wc[lane] = 0;
+        __syncwarp();
+        WCOUNT(P, 6, 1);
+#endif
         poly_init(P, cp, lane);
         // k nearest neighbours: each lane builds one plane in FP64, then all clip
         int emptied = 0;
@@ -923,6 +951,13 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
             double d2k = cp.knn_d2k[i];
             int okk = (int)cp.pos[cp.knn[i * cp.k + cp.k - 1]].w;
             bool done = traverse<R, MODE>(P, cp, i, yi, psii, an, d2k, okk, lane, bad, st);
+#ifdef SDOT_COUNTERS
+            __syncwarp();
+            if (lane < 8) atomicAdd(&cp.counters64[lane], (unsigned long long)P.wc[lane]);
+            __syncwarp();
+            if (lane < 8) P.wc[lane] = 0;
+            __syncwarp();
+#endif
             if (!done && MODE == MODE_CERTIFY && (st & CS_UNCERTIFIED)) {
                 if (lane == 0) {
                     int32_t q = atomicAdd(cp.queue_cnt, 1);
@@ -1144,9 +1179,13 @@ int evaluate_cells(DeviceState& d, const double* psi, int precision, EvalResult*
     cp.q64_cnt = d.counters + 1;
     SDOT_CUDA_TRY(cudaMemsetAsync(d.counters, 0, 8 * sizeof(int32_t), s));
 
-    cudaEvent_t e0, e1;
+    cudaEvent_t e0, e1, ep1, ep2;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    cudaEventCreate(&ep1);
+    cudaEventCreate(&ep2);
+    cp.counters64 = (unsigned long long*)(d.counters + 8);
+    SDOT_CUDA_TRY(cudaMemsetAsync(d.counters + 8, 0, 64, s));
     cudaEventRecord(e0, s);
     // pass 1: every cell, kNN planes + security test
     cp.work_counter = d.counters + 2;
@@ -1155,6 +1194,7 @@ int evaluate_cells(DeviceState& d, const double* psi, int precision, EvalResult*
     rc = precision == SDOT_PREC_FP64 ? launch_clip<double, MODE_CERTIFY>(cp, s)
                                      : launch_clip<float, MODE_CERTIFY>(cp, s);
     if (rc) return rc;
+    cudaEventRecord(ep1, s);
     int32_t cnt[2];
     SDOT_CUDA_TRY(cudaMemcpyAsync(cnt, d.counters, 8, cudaMemcpyDeviceToHost, s));
     SDOT_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1170,6 +1210,7 @@ int evaluate_cells(DeviceState& d, const double* psi, int precision, EvalResult*
         SDOT_CUDA_TRY(cudaMemcpyAsync(cnt, d.counters, 8, cudaMemcpyDeviceToHost, s));
         SDOT_CUDA_TRY(cudaStreamSynchronize(s));
     }
+    cudaEventRecord(ep2, s);
     int64_t reclipped = cnt[1];
     // pass 3 (mixed): FP64 re-clip of cells failing the FP32 checks
     if (precision != SDOT_PREC_FP64 && reclipped > 0) {
@@ -1189,8 +1230,14 @@ int evaluate_cells(DeviceState& d, const double* psi, int precision, EvalResult*
     SDOT_CUDA_TRY(cudaStreamSynchronize(s));
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventElapsedTime(&res->ms_pass[0], e0, ep1);
+    cudaEventElapsedTime(&res->ms_pass[1], ep1, ep2);
+    cudaEventElapsedTime(&res->ms_pass[2], ep2, e1);
+    SDOT_CUDA_TRY(cudaMemcpy(res->work, d.counters + 8, 64, cudaMemcpyDeviceToHost));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    cudaEventDestroy(ep1);
+    cudaEventDestroy(ep2);
     res->sum_vol = h[0];
     res->max_rel_err = h[1];
     res->l2_err = h[2];

@@ -94,6 +94,7 @@ struct DeviceState {
     int32_t* queue64;         // N, cells for the FP64 re-clip
     int32_t* counters;        // [0] requeue count [1] fp64 count [2] work counter
                               // [3] error flags [4] work counter 2 [5] work counter 3
+                              // [8..24) 64-bit diagnostic work counters
     // CSR (sorted order)
     int64_t* row_ptr;         // N + 1
     int32_t* col;             // nnz capacity N * (FCAP + 1)
@@ -149,6 +150,8 @@ struct EvalResult {
     int64_t requeued, reclipped, n_empty;
     uint32_t flags;
     float ms;
+    float ms_pass[3];             // certify pass, re-queue pass, FP64 re-clip pass
+    unsigned long long work[8];   // diagnostic work counters (zero unless compiled in)
 };
 int build_pyramid(DeviceState& d, const double* psi, cudaStream_t s);
 int evaluate_cells(DeviceState& d, const double* psi, int precision, EvalResult* res,
