@@ -1,0 +1,317 @@
+"""Benchmark: semi-discrete OT reconstruction on one GB300 (or N replicas).
+
+One step is one pass of the whole hot path on one synthetic box: grid hash + kNN
+(sdot_create), damped Newton to max|V - nu|/nu <= 1e-4 with every Laguerre
+evaluation, re-queue, FP64 re-clip, Hessian assembly and PCG solve (sdot_solve),
+and the displacement of every cell (sdot_displacement). The positions are already
+in device memory when the timed region starts; ``e2e`` repeats the measurement
+through the same C ABI with host buffers (host->device copy of the positions and
+device->host copy of the displacements inside the timed region).
+
+value = cells reconstructed per second (N / step time), summed over ranks.
+The default workload is the 256^3 Zel'dovich box with 5% clumped points (17.6 M
+seeds), mixed precision. ``--impl reference`` times the CPU oracle instead on a
+bounded sample of the same workload (certified cells at psi = 0, cells/s).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DEFAULT_WORKLOAD = "zeldovich-256^3-kinv-0.3a+clumps"
+FLOP_PER_CELL = 6000.0  # algorithmic FP32 work of one cell clip
+FP32_LANES_PER_SM = 128
+N_SM = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--tol", type=float, default=1e-4)
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="skip the single FP64 solve reported beside the mixed one")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def cpu_baseline(workload, seconds=12.0):
+    """The CPU oracle as it stands, on a bounded sample of the workload's cells."""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import sdot_oracle as O
+    from paper_2110_08868_gb300 import ics
+
+    y, nu, L = ics.make_config(**ics.CONFIGS[workload])
+    N = y.shape[0]
+    psi = np.zeros(N)
+    rng = np.random.default_rng(123)
+    cores = os.cpu_count() or 1
+    n = max(1, cores)
+    done = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        idx = rng.choice(N, n, replace=False)
+        O.cells(y, psi, L, "certified", idx=idx)
+        done += n
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "cells/s", "cores": cores, "kind": "oracle",
+            "sample": f"{done} certified oracle cells of the {workload} box (N={N}) at psi=0, "
+                      f"{dt:.1f} s on {cores} host threads"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    steps = []
+    base = None
+    for s in range(args.warmup + args.steps):
+        b = cpu_baseline(args.workload, seconds=8.0)
+        if s >= args.warmup:
+            steps.append(b["value"])
+        base = b
+    v = statistics.median(steps)
+    line = {"impl": "reference", "metric": "Laguerre cells/s", "value": v, "unit": "cells/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "psi": 0,
+                                             "mode": "certified oracle cells"},
+            "cpu_baseline": {"value": v, "unit": "cells/s", "cores": base["cores"],
+                             "kind": "oracle", "sample": base["sample"]},
+            "e2e": {"value": v, "unit": "cells/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_native(args, rank, world, local):
+    import torch
+
+    from paper_2110_08868_gb300 import binding as B
+    from paper_2110_08868_gb300 import ics
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    cfg = dict(ics.CONFIGS[args.workload])
+    if world > 1:
+        cfg["seed"] = cfg["seed"] + 1000 * rank  # replicas: one independent box per rank
+    y, nu, L = ics.make_config(**cfg)
+    N = int(y.shape[0])
+    box = [L, L, L]
+    pos_dev = torch.from_numpy(y).cuda()
+    disp_dev = torch.empty((N, 3), dtype=torch.float64, device="cuda")
+    opt = B.sdot_default_options(precision=args.precision)
+    stream = torch.cuda.current_stream()
+
+    def one_step(pos, disp):
+        rc, ctx = B.sdot_create(pos, None, box, opt)
+        B.check(rc)
+        try:
+            st = B.sdot_stats()
+            B.check(B.sdot_solve(ctx, args.tol, None, st))
+            B.check(B.sdot_displacement(ctx, disp))
+        finally:
+            B.sdot_destroy(ctx)
+        return st
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # warm-up
+    for _ in range(args.warmup):
+        one_step(pos_dev, disp_dev)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    l0 = B.sdot_kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        stats.append(one_step(pos_dev, disp_dev).as_dict())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = B.sdot_kernel_launches() - l0
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    t = torch.tensor([ms], dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * N / (ms_max / 1e3)
+
+    # e2e through host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        pos_host = torch.from_numpy(y).pin_memory()
+        disp_host = torch.empty((N, 3), dtype=torch.float64).pin_memory()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            one_step(pos_host, disp_host)
+        torch.cuda.synchronize()
+        e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+        te = torch.tensor([e_ms], dtype=torch.float64)
+        if dist is not None:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * N / (float(te.item()) / 1e3), "unit": "cells/s",
+               "h2d_bytes_per_step": N * 3 * 8, "d2h_bytes_per_step": N * 3 * 8}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    st = stats[-1]
+    evals = st["laguerre_evals"]
+    pass1_ms = st["ms_pass"][0] / max(evals, 1)
+    peaks = measured_peaks()
+    clock_ghz = (clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)) / 1e3
+    peak_tf = N_SM * FP32_LANES_PER_SM * 2 * clock_ghz / 1e3
+    achieved_tf = N * FLOP_PER_CELL / (pass1_ms / 1e3) / 1e12
+    roofline = {"kernel": "clip_kernel<float,certify> (first clipping pass)", "bound": "alu",
+                "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": achieved_tf / peak_tf, "traffic": None,
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {clock_ghz:.3f} GHz "
+                               "(median SM clock under load)",
+                "per_launch_ms": pass1_ms, "flop_per_cell": FLOP_PER_CELL}
+    extra = {"solve": {k: st[k] for k in ("newton_iters", "laguerre_evals", "cg_iters",
+                                          "max_rel_err", "requeued", "reclipped_fp64",
+                                          "ms_knn", "ms_clip", "ms_cg", "ms_total",
+                                          "ms_pass")}}
+    if not args.no_fp64_compare and args.precision == "mixed":
+        opt64 = B.sdot_default_options(precision="fp64")
+        rc, ctx = B.sdot_create(pos_dev, None, box, opt64)
+        B.check(rc)
+        s64 = B.sdot_stats()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B.check(B.sdot_solve(ctx, args.tol, None, s64))
+        torch.cuda.synchronize()
+        extra["fp64_solve_s"] = time.perf_counter() - t0
+        extra["fp64_solve"] = {k: s64.as_dict()[k] for k in ("newton_iters", "laguerre_evals",
+                                                             "ms_clip", "ms_cg", "ms_pass")}
+        B.sdot_destroy(ctx)
+    extra["mixed_solve_s"] = ms_max / 1e3
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.workload)
+    line = {"metric": "Laguerre cells/s", "value": value, "unit": "cells/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "N": N, "precision": args.precision,
+                       "tol": args.tol, "k": 24, "step": "create+solve+displacement",
+                       "l2": "inputs larger than L2 (device working set >> 129 MB)",
+                       "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
+            "cpu_baseline": cpu, "extra": extra}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_native(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -92,6 +92,8 @@ typedef struct {
     double ms_clip;          /* device time in cell clipping (all evaluations) */
     double ms_cg;            /* device time in PCG */
     double ms_total;         /* wall time of the solve */
+    double ms_pass[3];       /* device time per clipping pass, summed over evaluations:
+                                security-test pass, re-queue pass, FP64 re-clip pass */
 } sdot_stats;
 
 typedef struct sdot_ctx sdot_ctx;
@@ -170,6 +172,9 @@ int sdot_size(const sdot_ctx* ctx, int64_t* N, int* k);
 
 /* Release every resource of ctx (NULL is accepted). */
 void sdot_destroy(sdot_ctx* ctx);
+
+/* Number of kernel launches this library has issued in the process so far. */
+int64_t sdot_kernel_launches(void);
 
 /* Message of the last error on the calling thread ("" if none). */
 const char* sdot_last_error(void);

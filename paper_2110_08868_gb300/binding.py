@@ -47,16 +47,19 @@ class sdot_stats(ctypes.Structure):
                 ("last_alpha", ctypes.c_double), ("requeued", ctypes.c_int64),
                 ("reclipped_fp64", ctypes.c_int64), ("ms_knn", ctypes.c_double),
                 ("ms_clip", ctypes.c_double), ("ms_cg", ctypes.c_double),
-                ("ms_total", ctypes.c_double)]
+                ("ms_total", ctypes.c_double), ("ms_pass", ctypes.c_double * 3)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["ms_pass"] = list(self.ms_pass)
+        return d
 
 
 # every symbol include/sdot.h declares
 EXPORTS = ["sdot_default_options", "sdot_create", "sdot_set_stream", "sdot_laguerre",
            "sdot_solve", "sdot_csr_copy", "sdot_get_psi", "sdot_displacement", "sdot_knn",
-           "sdot_cell_status", "sdot_size", "sdot_destroy", "sdot_last_error"]
+           "sdot_cell_status", "sdot_size", "sdot_destroy", "sdot_kernel_launches",
+           "sdot_last_error"]
 
 _lib = None
 
@@ -89,10 +92,12 @@ def load(path=LIB_PATH):
     lib.sdot_size.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I)]
     lib.sdot_destroy.argtypes = [P]
     lib.sdot_destroy.restype = None
+    lib.sdot_kernel_launches.argtypes = []
+    lib.sdot_kernel_launches.restype = I64
     lib.sdot_last_error.argtypes = []
     lib.sdot_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("sdot_destroy", "sdot_last_error"):
+        if name not in ("sdot_destroy", "sdot_last_error", "sdot_kernel_launches"):
             getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -113,6 +118,10 @@ def _ptr(x, dtype=np.float64):
     if not isinstance(x, np.ndarray) or x.dtype != dtype or not x.flags.c_contiguous:
         raise TypeError(f"expected a C-contiguous numpy array of {np.dtype(dtype)}")
     return ctypes.c_void_p(x.ctypes.data)
+
+
+def sdot_kernel_launches():
+    return int(load().sdot_kernel_launches())
 
 
 def sdot_last_error():

@@ -170,6 +170,8 @@ extern "C" {
 
 const char* sdot_last_error(void) { return g_err.c_str(); }
 
+int64_t sdot_kernel_launches(void) { return (int64_t)launch_count(); }
+
 int sdot_default_options(sdot_options* o) {
     if (!o) return SDOT_ERR_ARG;
     o->k = 24;
@@ -256,7 +258,8 @@ int sdot_create(const double* pos, const double* mass, int64_t N, const double b
         G[a] = (int)g;
         ncell *= G[a];
     }
-    if ((rc = alloc_n(c, &d.pos, N)) || (rc = alloc_n(c, &d.posf, N)) ||
+    if ((rc = alloc_n(c, &d.pos, N)) || (rc = alloc_n(c, &d.posf, N)) || (rc = alloc_n(c, &d.pslo, N)) ||
+        (rc = alloc_n(c, &d.leafc, N)) ||
         (rc = alloc_n(c, &d.perm, N)) || (rc = alloc_n(c, &d.iperm, N)) ||
         (rc = alloc_n(c, &d.nu, N)) || (rc = alloc_n(c, &d.psi, N)) ||
         (rc = alloc_n(c, &d.psi_trial, N)) || (rc = alloc_n(c, &d.knn, N * d.k)) ||
@@ -432,6 +435,7 @@ int sdot_solve(sdot_ctx* c, double tol, const double* psi0, sdot_stats* st) {
     c->eval_valid = true;
     S.laguerre_evals = 1;
     S.ms_clip += ev.ms;
+    for (int q = 0; q < 3; q++) S.ms_pass[q] += ev.ms_pass[q];
     if ((rc = eval_status(ev, "sdot_solve"))) return rc;
     if (ev.n_empty > 0) {
         set_error("sdot_solve: the initial psi has empty cells");
@@ -473,6 +477,7 @@ int sdot_solve(sdot_ctx* c, double tol, const double* psi0, sdot_stats* st) {
             trials++;
             S.laguerre_evals++;
             S.ms_clip += et.ms;
+            for (int q = 0; q < 3; q++) S.ms_pass[q] += et.ms_pass[q];
             bool valid = !(et.flags & (CS_TOO_LARGE | CS_CAPACITY));
             if (valid && et.min_vol >= eps0 && et.l2_err <= (1.0 - 0.5 * alpha) * ev.l2_err) break;
             alpha *= 0.5;

@@ -105,6 +105,9 @@ struct ClipParams {
     const int32_t* worklist;  // null: cells 0..nwork-1
     int64_t nwork;
     unsigned long long* counters64;  // diagnostic work counters (8)
+    const float* pslo;               // low part of psi/a^2
+    const int32_t* leafc;            // grid cell of each seed, x | y << 10 | z << 20
+    int facets_valid;                // fcnt/fcol hold the previous diagram's facets
 };
 
 __device__ __forceinline__ double wrapd(double dx, double L, double halfL) {
@@ -303,12 +306,15 @@ __device__ __noinline__ int poly_clip(WarpPoly<R>& P, const V4<R>& pn, R plen, i
     for (int t = 0; t < SL; t++) {
         int s = lane + 32 * t;
         out[t] = false;
-        if (s < nt) {
-            R sd;
-            out[t] = beyond(P.v[s], pn, plen, sd);
+        m[t] = 0u;
+        if (32 * t < nt) {  // warp-uniform
+            if (s < nt) {
+                R sd;
+                out[t] = beyond(P.v[s], pn, plen, sd);
+            }
+            m[t] = __ballot_sync(FULLMASK, out[t]);
+            nrem += __popc(m[t]);
         }
-        m[t] = __ballot_sync(FULLMASK, out[t]);
-        nrem += __popc(m[t]);
     }
     WCOUNT(P, 0, 1);
     if (nrem == 0) return CLIP_NONE;
@@ -416,15 +422,17 @@ __device__ __noinline__ int poly_clip(WarpPoly<R>& P, const V4<R>& pn, R plen, i
 #pragma unroll
         for (int t = 0; t < SL; t++) {
             int s = lane + 32 * t;
-            bool keep = s < nt && !out[t];
-            uint32_t km = __ballot_sync(FULLMASK, keep);
             dst[t] = -1;
-            if (keep) {
-                kt[t] = P.tri[s];
-                kv[t] = P.v[s];
-                dst[t] = base + __popc(km & below);
+            if (32 * t < nt) {  // warp-uniform
+                bool keep = s < nt && !out[t];
+                uint32_t km = __ballot_sync(FULLMASK, keep);
+                if (keep) {
+                    kt[t] = P.tri[s];
+                    kv[t] = P.v[s];
+                    dst[t] = base + __popc(km & below);
+                }
+                base += __popc(km);
             }
-            base += __popc(km);
         }
         __syncwarp();
 #pragma unroll
@@ -472,6 +480,53 @@ __device__ __forceinline__ void make_plane(const ClipParams& cp, const Pos4& yi,
     w = 0.5 * (nx * nx + ny * ny + nz * nz) + (psii - cp.psi[j]) * cp.inv_a2;
 }
 
+// The cell's own seed in grid-local form: integer grid cell and FP32 offset from the
+// grid cell's corner (units of a), psi/a^2 split into two floats (hi + lo).
+struct SeedRef {
+    int c[3];
+    float off[3];
+    float phi, plo;
+};
+
+__device__ __forceinline__ SeedRef load_seed(const ClipParams& cp, int64_t i) {
+    SeedRef r;
+    float4 p = cp.posf[i];
+    int lc = cp.leafc[i];
+    r.c[0] = lc & 1023;
+    r.c[1] = (lc >> 10) & 1023;
+    r.c[2] = (lc >> 20) & 1023;
+    r.off[0] = p.x;
+    r.off[1] = p.y;
+    r.off[2] = p.z;
+    r.phi = p.w;
+    r.plo = cp.pslo[i];
+    return r;
+}
+
+// FP32 plane of seed j for cell i from grid-local coordinates: the integer part of
+// the difference is exact, so the plane is accurate to FP32 relative precision of
+// |d| and of the psi difference (psi carried as hi + lo floats).
+__device__ __forceinline__ void plane_f32(const ClipParams& cp, const SeedRef& si, int32_t j,
+                                          float& nx, float& ny, float& nz, float& w) {
+    float4 pj = cp.posf[j];
+    int lc = cp.leafc[j];
+    int cj[3] = {lc & 1023, (lc >> 10) & 1023, (lc >> 20) & 1023};
+    float oj[3] = {pj.x, pj.y, pj.z};
+    float d[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        int dc = cj[a] - si.c[a];
+        if (2 * dc > cp.G[a]) dc -= cp.G[a];
+        else if (2 * dc < -cp.G[a]) dc += cp.G[a];
+        float v = (float)dc * cp.ht[a] + (oj[a] - si.off[a]);
+        d[a] = wrapf(v, cp.Lt[a], cp.halfLt[a]);
+    }
+    nx = d[0];
+    ny = d[1];
+    nz = d[2];
+    w = 0.5f * (nx * nx + ny * ny + nz * nz) + ((si.phi - pj.w) + (si.plo - cp.pslo[j]));
+}
+
 __device__ __forceinline__ float circ_gap(float p, float lo, float hi, float Lt) {
     // distance from p to the interval [lo, hi] on a circle of length Lt
     if (p >= lo && p <= hi) return 0.f;
@@ -492,17 +547,65 @@ __device__ __forceinline__ float circ_far(float p, float lo, float hi, float Lt)
     return fmaxf(e1, e2);
 }
 
-struct Anchor {
-    float z[3];      // anchor, local (units of a)
-    float zabs[3];   // anchor, absolute (units of a), wrapped
-    float yabs[3];   // seed, absolute (units of a)
-    float z2h;       // 1/2 |z|^2
-    float psi_i;     // psi_i / a^2
+// Current bounds of the polytope: box [bmin, bmax], its centre c and the radius Rc of
+// the smallest ball around c holding every vertex (local coordinates, units of a).
+struct Bounds {
+    float bmin[3], bmax[3];
+    float c[3];
+    float Rc;
+    float cabs[3];  // c in absolute coordinates, wrapped into the box
+    float yabs[3];  // the seed in absolute coordinates
+    float c2h;      // 1/2 |c|^2
+    float psi_i;    // psi_i / a^2 (hi part)
 };
 
-// true when every seed of node (level l, coordinates X, Y, Z) provably cannot cut
-__device__ __forceinline__ bool node_pruned(const ClipParams& cp, const Anchor& an, float Rz,
-                                            int l, int X, int Y, int Z) {
+template <typename R>
+__device__ void poly_bounds(const WarpPoly<R>& P, const ClipParams& cp, Bounds& b, int lane) {
+    float mn[3] = {1e30f, 1e30f, 1e30f}, mx[3] = {-1e30f, -1e30f, -1e30f};
+    for (int s = lane; s < P.nt; s += 32) {
+        V3<R> v = P.v[s];
+        float vv[3] = {(float)v.x, (float)v.y, (float)v.z};
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            mn[a] = fminf(mn[a], vv[a]);
+            mx[a] = fmaxf(mx[a], vv[a]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[a] = fminf(mn[a], __shfl_xor_sync(FULLMASK, mn[a], o));
+            mx[a] = fmaxf(mx[a], __shfl_xor_sync(FULLMASK, mx[a], o));
+        }
+        b.bmin[a] = mn[a];
+        b.bmax[a] = mx[a];
+        b.c[a] = 0.5f * (mn[a] + mx[a]);
+    }
+    float r2 = 0.f;
+    for (int s = lane; s < P.nt; s += 32) {
+        V3<R> v = P.v[s];
+        float dx = (float)v.x - b.c[0], dy = (float)v.y - b.c[1], dz = (float)v.z - b.c[2];
+        r2 = fmaxf(r2, dx * dx + dy * dy + dz * dz);
+    }
+    r2 = warp_max(r2);
+    b.Rc = sqrtf(r2) * 1.0001f + 1e-5f;
+    b.c2h = 0.5f * (b.c[0] * b.c[0] + b.c[1] * b.c[1] + b.c[2] * b.c[2]);
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        float za = b.yabs[a] + b.c[a];
+        za = fmodf(za, cp.Lt[a]);
+        if (za < 0.f) za += cp.Lt[a];
+        if (za >= cp.Lt[a]) za = 0.f;
+        b.cabs[a] = za;
+    }
+}
+
+// true when every seed of node (level l, coordinates X, Y, Z) provably cannot cut:
+// for a seed j in the node, c.d + Rc |d| <= 1/2|d|^2 + psi_i - psi_j follows from
+// 1/2 u^2 - 1/2|c|^2 - Rc dmax - (psimax - psi_i) >= 0 with u the distance from the
+// anchor c to the node and dmax the largest distance from the seed to the node.
+__device__ __forceinline__ bool node_pruned(const ClipParams& cp, const Bounds& b, int l, int X,
+                                            int Y, int Z) {
     float pm = cp.pyr.psimax[cp.pyr.off[l] +
                              ((int64_t)Z * cp.pyr.dim[l][1] + Y) * cp.pyr.dim[l][0] + X];
     if (pm == -INFINITY) return true;  // no seed inside
@@ -513,152 +616,180 @@ __device__ __forceinline__ bool node_pruned(const ClipParams& cp, const Anchor& 
     for (int a = 0; a < 3; a++) {
         int c0 = c[a] * span, c1 = min((c[a] + 1) * span, cp.G[a]);
         float lo = c0 * cp.ht[a], hi = (c1 == cp.G[a]) ? cp.Lt[a] : c1 * cp.ht[a];
-        float g = circ_gap(an.zabs[a], lo, hi, cp.Lt[a]);
-        float f = circ_far(an.yabs[a], lo, hi, cp.Lt[a]);
+        float g = circ_gap(b.cabs[a], lo, hi, cp.Lt[a]);
+        float f = circ_far(b.yabs[a], lo, hi, cp.Lt[a]);
         u2 += g * g;
         dm2 += f * f;
     }
     float dmax = sqrtf(dm2);
-    float t1 = 0.5f * u2, t2 = Rz * dmax, dpsi = pm - an.psi_i;
-    float val = t1 - an.z2h - t2 - dpsi;
-    float margin = 1e-5f * (t1 + an.z2h + t2 + fabsf(pm) + fabsf(an.psi_i)) + 1e-6f;
+    float t1 = 0.5f * u2, t2 = b.Rc * dmax, dpsi = pm - b.psi_i;
+    float val = t1 - b.c2h - t2 - dpsi;
+    float margin = 2e-5f * (t1 + b.c2h + t2 + fabsf(pm) + fabsf(b.psi_i)) + 1e-5f;
     return val > margin;
 }
 
-// conservative FP32 test: can seed j's plane reach the polytope (anchor z, radius Rz)
-__device__ __forceinline__ bool seed_may_cut(const ClipParams& cp, const Anchor& an, float Rz,
-                                             const float4& yj) {
-    float dx = wrapf(yj.x - an.yabs[0], cp.Lt[0], cp.halfLt[0]);
-    float dy = wrapf(yj.y - an.yabs[1], cp.Lt[1], cp.halfLt[1]);
-    float dz = wrapf(yj.z - an.yabs[2], cp.Lt[2], cp.halfLt[2]);
-    float d2 = dx * dx + dy * dy + dz * dz;
-    float dl = sqrtf(d2);
-    float b = 0.5f * d2 + an.psi_i - yj.w;
-    float lhs = an.z[0] * dx + an.z[1] * dy + an.z[2] * dz + Rz * dl;
-    float margin = 1e-5f * (fabsf(lhs) + 0.5f * d2 + fabsf(an.psi_i) + fabsf(yj.w)) + 1e-6f;
-    return lhs > b - margin;
+// conservative FP32 test: can the plane (n, w) reach the polytope's bounding box?
+__device__ __forceinline__ bool box_may_cut(const Bounds& b, float nx, float ny, float nz,
+                                            float w) {
+    float sx = nx > 0.f ? nx * b.bmax[0] : nx * b.bmin[0];
+    float sy = ny > 0.f ? ny * b.bmax[1] : ny * b.bmin[1];
+    float sz = nz > 0.f ? nz * b.bmax[2] : nz * b.bmin[2];
+    float S = sx + sy + sz;
+    float margin = 2e-5f * (fabsf(sx) + fabsf(sy) + fabsf(sz) + fabsf(w)) + 1e-5f;
+    return S > w - margin;
 }
 
 enum { MODE_CERTIFY = 0, MODE_FULL = 1 };
 enum { LEAF_OK = 0, LEAF_STOP = 1 };
 
-// Test every seed of one grid cell against the polytope. MODE_CERTIFY: stop at the
-// first unseen seed whose plane cuts. MODE_FULL: clip by every such seed.
+struct CellCtx {
+    int64_t i;
+    Pos4 yi;      // FP64 seed (FP64 planes)
+    double psii;  // FP64 psi_i
+    SeedRef si;   // grid-local seed (FP32 planes)
+};
+
+template <typename R>
+__device__ __forceinline__ void build_plane(const ClipParams& cp, const CellCtx& cc, int32_t j,
+                                            V4<R>& pn, R& plen) {
+    if (sizeof(R) == 8) {
+        double nxd, nyd, nzd, wd;
+        make_plane(cp, cc.yi, cc.psii, j, nxd, nyd, nzd, wd);
+        pn.x = (R)nxd;
+        pn.y = (R)nyd;
+        pn.z = (R)nzd;
+        pn.w = (R)wd;
+    } else {
+        float nx, ny, nz, w;
+        plane_f32(cp, cc.si, j, nx, ny, nz, w);
+        pn.x = (R)nx;
+        pn.y = (R)ny;
+        pn.z = (R)nz;
+        pn.w = (R)w;
+    }
+    plen = sqrt(pn.x * pn.x + pn.y * pn.y + pn.z * pn.z);
+}
+
+// One candidate seed j (warp-uniform): skip it if it already is a plane of the
+// polytope or its plane leaves every vertex inside; otherwise CERTIFY fails and FULL
+// clips. Returns LEAF_STOP when the cell's processing must stop.
 template <typename R, int MODE>
-__device__ __noinline__ int process_leaf(WarpPoly<R>& P, const ClipParams& cp, int64_t i, const Pos4& yi,
-                            double psii, const Anchor& an, float& Rz, const V3<R>& zr,
-                            double d2k, int ok_k, int lane, bool& bad, uint32_t& st,
-                            int64_t leaf) {
-    int32_t sb = cp.cell_start[leaf], se = cp.cell_start[leaf + 1];
-    WCOUNT(P, 3, 1);
-    WCOUNT(P, 4, se - sb);
-    for (int32_t s0 = sb; s0 < se; s0 += 32) {
-        int32_t s = s0 + lane;
+__device__ int candidate(WarpPoly<R>& P, const ClipParams& cp, const CellCtx& cc, Bounds& b,
+                         int32_t j, int lane, bool& bad, uint32_t& st) {
+    bool dup = false;
+#pragma unroll
+    for (int w = 0; w < MAXP / 32; w++)
+        dup |= (lane + 32 * w < P.np && P.pj[lane + 32 * w] == j);
+    if (__any_sync(FULLMASK, dup)) return LEAF_OK;
+    V4<R> pn;
+    R plen;
+    build_plane(cp, cc, j, pn, plen);
+    if (MODE == MODE_CERTIFY) {
+        bool o = false;
+        for (int q = lane; q < P.nt; q += 32) {
+            R sd;
+            o |= beyond(P.v[q], pn, plen, sd);
+        }
+        if (__any_sync(FULLMASK, o)) {
+            st |= CS_UNCERTIFIED;
+            return LEAF_STOP;
+        }
+        return LEAF_OK;
+    }
+    int rc = poly_clip(P, pn, plen, j, lane, bad);
+    if (rc == CLIP_EMPTY) {
+        st |= CS_EMPTY;
+        return LEAF_STOP;
+    }
+    if (rc == CLIP_CAP) {
+        st |= CS_CAPACITY | CS_CAP_POLY;
+        return LEAF_STOP;
+    }
+    if (rc == CLIP_CUT) poly_bounds(P, cp, b, lane);
+    return LEAF_OK;
+}
+
+// The seeds of up to 32 grid cells at once, one grid cell per lane (leaf < 0: none).
+template <typename R, int MODE>
+__device__ __noinline__ int process_leaves(WarpPoly<R>& P, const ClipParams& cp,
+                                           const CellCtx& cc, Bounds& b, int64_t leaf, int lane,
+                                           bool& bad, uint32_t& st) {
+    int32_t sb = 0, se = 0;
+    if (leaf >= 0) {
+        sb = cp.cell_start[leaf];
+        se = cp.cell_start[leaf + 1];
+    }
+    int n = se - sb;
+    int maxn = n;
+    for (int o = 16; o > 0; o >>= 1) maxn = max(maxn, __shfl_xor_sync(FULLMASK, maxn, o));
+    WCOUNT(P, 3, __popc(__ballot_sync(FULLMASK, leaf >= 0)));
+    for (int u = 0; u < maxn; u++) {
+        int32_t s = sb + u;
         bool cand = false;
-        if (s < se && s != (int32_t)i) cand = seed_may_cut(cp, an, Rz, cp.posf[s]);
+        if (u < n && s != (int32_t)cc.i) {
+            float nx, ny, nz, w;
+            plane_f32(cp, cc.si, s, nx, ny, nz, w);
+            cand = box_may_cut(b, nx, ny, nz, w);
+        }
+        WCOUNT(P, 4, __popc(__ballot_sync(FULLMASK, u < n)));
         uint32_t cm = __ballot_sync(FULLMASK, cand);
         WCOUNT(P, 5, __popc(cm));
         while (cm) {
-            int c = __ffs(cm) - 1;
+            int src = __ffs(cm) - 1;
             cm &= cm - 1;
-            int32_t j = s0 + c;
-            // seen in the kNN list?
-            Pos4 yj = cp.pos[j];
-            double d2 = exact_d2(yi, yj, cp);
-            int oj = (int)yj.w;
-            if (d2 < d2k || (d2 == d2k && oj <= ok_k)) continue;
-            // already a plane of the polytope?
-            bool dup = false;
-#pragma unroll
-            for (int w = 0; w < MAXP / 32; w++)
-                dup |= (lane + 32 * w < P.np && P.pj[lane + 32 * w] == j);
-            if (__any_sync(FULLMASK, dup)) continue;
-            double nxd, nyd, nzd, wd;
-            make_plane(cp, yi, psii, j, nxd, nyd, nzd, wd);
-            V4<R> pn;
-            pn.x = (R)nxd;
-            pn.y = (R)nyd;
-            pn.z = (R)nzd;
-            pn.w = (R)wd;
-            R plen = (R)sqrt(nxd * nxd + nyd * nyd + nzd * nzd);
-            if (MODE == MODE_CERTIFY) {
-                bool o = false;
-                for (int q = lane; q < P.nt; q += 32) {
-                    R sd;
-                    o |= beyond(P.v[q], pn, plen, sd);
-                }
-                if (__any_sync(FULLMASK, o)) {
-                    st |= CS_UNCERTIFIED;
-                    return LEAF_STOP;
-                }
-            } else {
-                int rc = poly_clip(P, pn, plen, j, lane, bad);
-                if (rc == CLIP_EMPTY) {
-                    st |= CS_EMPTY;
-                    return LEAF_STOP;
-                }
-                if (rc == CLIP_CAP) {
-                    st |= CS_CAPACITY | CS_CAP_POLY;
-                    return LEAF_STOP;
-                }
-                if (rc == CLIP_CUT) Rz = (float)poly_radius(P, zr, lane) * 1.0001f + 1e-6f;
-            }
+            int32_t j = __shfl_sync(FULLMASK, s, src);
+            if (candidate<R, MODE>(P, cp, cc, b, j, lane, bad, st) == LEAF_STOP) return LEAF_STOP;
         }
     }
     return LEAF_OK;
 }
 
-// Near-first pass for re-queued cells: clip by the seeds of the grid cells in
-// Chebyshev rings around the anchor's grid cell, so the polytope is small before the
-// pyramid walk (which visits nodes in no particular order) starts.
+// Near-first pass for re-queued cells: the grid cells in Chebyshev rings around the
+// grid cell of the previous centroid, so the polytope is small before the pyramid
+// walk (which visits nodes in no particular order) starts.
 template <typename R>
-__device__ __noinline__ bool ring_walk(WarpPoly<R>& P, const ClipParams& cp, int64_t i, const Pos4& yi,
-                          double psii, const Anchor& an, const V3<R>& zr, double d2k, int ok_k,
-                          int lane, bool& bad, uint32_t& st) {
+__device__ __noinline__ bool ring_walk(WarpPoly<R>& P, const ClipParams& cp, const CellCtx& cc,
+                                       Bounds& b, const float* zprev, int lane, bool& bad,
+                                       uint32_t& st) {
     int ca[3];
     float hmin = 1e30f;
     for (int a = 0; a < 3; a++) {
-        int c = (int)floorf(an.zabs[a] / cp.ht[a]);
+        float za = fmodf(b.yabs[a] + zprev[a], cp.Lt[a]);
+        if (za < 0.f) za += cp.Lt[a];
+        int c = (int)floorf(za / cp.ht[a]);
         ca[a] = c < 0 ? 0 : (c >= cp.G[a] ? cp.G[a] - 1 : c);
         hmin = fminf(hmin, cp.ht[a]);
     }
     const int Gmin = min(cp.G[0], min(cp.G[1], cp.G[2]));
-    float Rz = (float)poly_radius(P, zr, lane) * 1.0001f + 1e-6f;
     for (int r = 0; r <= 3; r++) {
         if (2 * r + 1 > Gmin) break;
-        if (r >= 2 && (float)(r - 1) * hmin > 2.f * Rz) break;
-        for (int oz = -r; oz <= r; oz++)
-            for (int oy = -r; oy <= r; oy++) {
-                bool face = (oz == -r || oz == r || oy == -r || oy == r);
-                int step = (face || r == 0) ? 1 : 2 * r;
-                for (int ox = -r; ox <= r; ox += step) {
+        if (r >= 2 && (float)(r - 1) * hmin > 2.f * b.Rc) break;
+        const int w = 2 * r + 1, n3 = w * w * w;
+        for (int base = 0; base < n3; base += 32) {
+            int t = base + lane;
+            int64_t leaf = -1;
+            if (t < n3) {
+                int ox = t % w - r, oy = (t / w) % w - r, oz = t / (w * w) - r;
+                int ch = max(abs(ox), max(abs(oy), abs(oz)));
+                if (ch == r) {
                     int cx = ((ca[0] + ox) % cp.G[0] + cp.G[0]) % cp.G[0];
                     int cy = ((ca[1] + oy) % cp.G[1] + cp.G[1]) % cp.G[1];
                     int cz = ((ca[2] + oz) % cp.G[2] + cp.G[2]) % cp.G[2];
-                    int64_t leaf = ((int64_t)cz * cp.G[1] + cy) * cp.G[0] + cx;
-                    if (process_leaf<R, MODE_FULL>(P, cp, i, yi, psii, an, Rz, zr, d2k, ok_k, lane,
-                                                   bad, st, leaf) == LEAF_STOP)
-                        return false;
+                    leaf = ((int64_t)cz * cp.G[1] + cy) * cp.G[0] + cx;
                 }
             }
+            if (process_leaves<R, MODE_FULL>(P, cp, cc, b, leaf, lane, bad, st) == LEAF_STOP)
+                return false;
+        }
     }
     return true;
 }
 
-// Walk the pyramid. MODE_CERTIFY: return false as soon as an unseen seed cuts the
-// polytope. MODE_FULL: clip every such seed. Returns true when the walk completed.
+// Walk the pyramid. MODE_CERTIFY: return false as soon as a seed cuts the polytope.
+// MODE_FULL: clip every such seed. Returns true when the walk completed.
 template <typename R, int MODE>
-__device__ bool traverse(WarpPoly<R>& P, const ClipParams& cp, int64_t i, const Pos4& yi,
-                         double psii, const Anchor& an, double d2k, int ok_k, int lane,
-                         bool& bad, uint32_t& st) {
-    V3<R> zr;
-    zr.x = (R)an.z[0];
-    zr.y = (R)an.z[1];
-    zr.z = (R)an.z[2];
-    if (MODE == MODE_FULL) {
-        if (!ring_walk(P, cp, i, yi, psii, an, zr, d2k, ok_k, lane, bad, st)) return false;
-    }
-    float Rz = (float)poly_radius(P, zr, lane) * 1.0001f + 1e-6f;
+__device__ bool traverse(WarpPoly<R>& P, const ClipParams& cp, const CellCtx& cc, Bounds& b,
+                         int lane, bool& bad, uint32_t& st) {
     const int top = cp.pyr.nlev;  // virtual root level
     int sp = 0;
     if (lane == 0) P.stack[0] = (uint32_t)top << 27;
@@ -699,7 +830,7 @@ __device__ bool traverse(WarpPoly<R>& P, const ClipParams& cp, int64_t i, const 
                 cx = x0 + t % nx;
                 cy = y0 + (t / nx) % ny;
                 cz = z0 + t / (nx * ny);
-                surv = !node_pruned(cp, an, Rz, cl, cx, cy, cz);
+                surv = !node_pruned(cp, b, cl, cx, cy, cz);
             }
             uint32_t sm = __ballot_sync(FULLMASK, surv);
             if (sm == 0) continue;
@@ -712,24 +843,15 @@ __device__ bool traverse(WarpPoly<R>& P, const ClipParams& cp, int64_t i, const 
                 uint32_t below = (lane == 0) ? 0u : ((1u << lane) - 1u);
                 if (surv)
                     P.stack[sp + __popc(sm & below)] =
-                        ((uint32_t)cl << 27) |
-                        (uint32_t)(((int64_t)cz * cdy + cy) * cdx + cx);
+                        ((uint32_t)cl << 27) | (uint32_t)(((int64_t)cz * cdy + cy) * cdx + cx);
                 sp += n;
                 __syncwarp();
                 continue;
             }
-            // surviving leaves: test their seeds
-            while (sm) {
-                int src = __ffs(sm) - 1;
-                sm &= sm - 1;
-                int lx = __shfl_sync(FULLMASK, cx, src);
-                int ly = __shfl_sync(FULLMASK, cy, src);
-                int lz = __shfl_sync(FULLMASK, cz, src);
-                int64_t leaf = ((int64_t)lz * cp.G[1] + ly) * cp.G[0] + lx;
-                if (process_leaf<R, MODE>(P, cp, i, yi, psii, an, Rz, zr, d2k, ok_k, lane, bad, st,
-                                          leaf) == LEAF_STOP)
-                    return false;
-            }
+            // surviving leaves: their seeds, one leaf per lane
+            int64_t leaf = surv ? ((int64_t)cz * cp.G[1] + cy) * cp.G[0] + cx : -1;
+            if (process_leaves<R, MODE>(P, cp, cc, b, leaf, lane, bad, st) == LEAF_STOP)
+                return false;
         }
     }
     return true;
@@ -870,6 +992,37 @@ __device__ __noinline__ void integrate(WarpPoly<R>& P, const ClipParams& cp, int
     }
 }
 
+// clip by a list of seeds (warp-uniform count): each lane builds one plane, then the
+// warp clips by them in order
+template <typename R>
+__device__ int clip_list(WarpPoly<R>& P, const ClipParams& cp, const CellCtx& cc,
+                         const int32_t* list, int n, int lane, bool& bad) {
+    for (int t0 = 0; t0 < n; t0 += 32) {
+        int t = t0 + lane;
+        V4<R> pl;
+        pl.x = pl.y = pl.z = pl.w = R(0);
+        R len = R(1);
+        int32_t j = -1;
+        if (t < n) {
+            j = list[t];
+            build_plane(cp, cc, j, pl, len);
+        }
+        int nk = min(32, n - t0);
+        for (int u = 0; u < nk; u++) {
+            V4<R> pn;
+            pn.x = __shfl_sync(FULLMASK, pl.x, u);
+            pn.y = __shfl_sync(FULLMASK, pl.y, u);
+            pn.z = __shfl_sync(FULLMASK, pl.z, u);
+            pn.w = __shfl_sync(FULLMASK, pl.w, u);
+            R plen = __shfl_sync(FULLMASK, len, u);
+            int32_t ju = __shfl_sync(FULLMASK, j, u);
+            int rc = poly_clip(P, pn, plen, ju, lane, bad);
+            if (rc == CLIP_EMPTY || rc == CLIP_CAP) return rc;
+        }
+    }
+    return CLIP_NONE;
+}
+
 template <typename R, int MODE>
 __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
     clip_kernel(ClipParams cp) {
@@ -881,8 +1034,9 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
     float psimax_glob = -INFINITY;
     {
         int tl = cp.pyr.nlev - 1;
-        int nt = cp.pyr.dim[tl][0] * cp.pyr.dim[tl][1] * cp.pyr.dim[tl][2];
-        for (int t = lane; t < nt; t += 32) psimax_glob = fmaxf(psimax_glob, cp.pyr.psimax[cp.pyr.off[tl] + t]);
+        int ntop = cp.pyr.dim[tl][0] * cp.pyr.dim[tl][1] * cp.pyr.dim[tl][2];
+        for (int t = lane; t < ntop; t += 32)
+            psimax_glob = fmaxf(psimax_glob, cp.pyr.psimax[cp.pyr.off[tl] + t]);
         psimax_glob = warp_max(psimax_glob);
     }
     const float halfLmin = 0.5f * fminf(cp.Lt[0], fminf(cp.Lt[1], cp.Lt[2]));
@@ -891,9 +1045,12 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
         if (lane == 0) w = atomicAdd(cp.work_counter, 1);
         w = __shfl_sync(FULLMASK, w, 0);
         if (w >= cp.nwork) break;
-        const int64_t i = cp.worklist ? cp.worklist[w] : w;
-        const Pos4 yi = cp.pos[i];
-        const double psii = cp.psi[i];
+        CellCtx cc;
+        cc.i = cp.worklist ? cp.worklist[w] : w;
+        const int64_t i = cc.i;
+        cc.yi = cp.pos[i];
+        cc.psii = cp.psi[i];
+        cc.si = load_seed(cp, i);
         bool bad = false;
         uint32_t st = 0;
 #ifdef SDOT_COUNTERS
@@ -902,55 +1059,28 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
         WCOUNT(P, 6, 1);
 #endif
         poly_init(P, cp, lane);
-        // k nearest neighbours: each lane builds one plane in FP64, then all clip
-        int emptied = 0;
-        for (int t0 = 0; t0 < cp.k; t0 += 32) {
-            int t = t0 + lane;
-            double nxd = 0, nyd = 0, nzd = 0, wd = 0;
-            int32_t j = -1;
-            if (t < cp.k) {
-                j = cp.knn[i * cp.k + t];
-                make_plane(cp, yi, psii, j, nxd, nyd, nzd, wd);
-            }
-            int nk = min(32, cp.k - t0);
-            for (int u = 0; u < nk; u++) {
-                V4<R> pn;
-                pn.x = (R)__shfl_sync(FULLMASK, nxd, u);
-                pn.y = (R)__shfl_sync(FULLMASK, nyd, u);
-                pn.z = (R)__shfl_sync(FULLMASK, nzd, u);
-                pn.w = (R)__shfl_sync(FULLMASK, wd, u);
-                int32_t ju = __shfl_sync(FULLMASK, j, u);
-                R plen = sqrt(pn.x * pn.x + pn.y * pn.y + pn.z * pn.z);
-                int rc = poly_clip(P, pn, plen, ju, lane, bad);
-                if (rc == CLIP_EMPTY) { emptied = 1; break; }
-                if (rc == CLIP_CAP) { st |= CS_CAPACITY | CS_CAP_POLY; break; }
-            }
-            if (emptied || (st & CS_CAPACITY)) break;
+        // first candidates: the cell's facets in the previous diagram, then its k
+        // nearest seeds
+        int rc = CLIP_NONE;
+        if (cp.facets_valid) {
+            int nprev = min(cp.fcnt[i], FCAP);
+            rc = clip_list(P, cp, cc, cp.fcol + i * FCAP, nprev, lane, bad);
         }
-        if (emptied) st |= CS_EMPTY;
+        if (rc == CLIP_NONE || rc == CLIP_CUT)
+            rc = clip_list(P, cp, cc, cp.knn + i * cp.k, cp.k, lane, bad);
+        if (rc == CLIP_EMPTY) st |= CS_EMPTY;
+        if (rc == CLIP_CAP) st |= CS_CAPACITY | CS_CAP_POLY;
+        float zprev[3] = {cp.anchor[3 * i], cp.anchor[3 * i + 1], cp.anchor[3 * i + 2]};
+        if (!(isfinite(zprev[0]) && isfinite(zprev[1]) && isfinite(zprev[2])))
+            zprev[0] = zprev[1] = zprev[2] = 0.f;
         if (!st) {
-            Anchor an;
-            float4 yf = cp.posf[i];
-            an.yabs[0] = yf.x;
-            an.yabs[1] = yf.y;
-            an.yabs[2] = yf.z;
-            an.psi_i = yf.w;
-            float z0 = cp.anchor[3 * i], z1 = cp.anchor[3 * i + 1], z2 = cp.anchor[3 * i + 2];
-            if (!(isfinite(z0) && isfinite(z1) && isfinite(z2))) z0 = z1 = z2 = 0.f;
-            an.z[0] = z0;
-            an.z[1] = z1;
-            an.z[2] = z2;
-            an.z2h = 0.5f * (z0 * z0 + z1 * z1 + z2 * z2);
-            for (int a = 0; a < 3; a++) {
-                float za = an.yabs[a] + an.z[a];
-                za = fmodf(za, cp.Lt[a]);
-                if (za < 0.f) za += cp.Lt[a];
-                if (za >= cp.Lt[a]) za = 0.f;
-                an.zabs[a] = za;
-            }
-            double d2k = cp.knn_d2k[i];
-            int okk = (int)cp.pos[cp.knn[i * cp.k + cp.k - 1]].w;
-            bool done = traverse<R, MODE>(P, cp, i, yi, psii, an, d2k, okk, lane, bad, st);
+            Bounds b;
+            for (int a = 0; a < 3; a++) b.yabs[a] = (float)cc.si.c[a] * cp.ht[a] + cc.si.off[a];
+            b.psi_i = cc.si.phi;
+            poly_bounds(P, cp, b, lane);
+            bool done = true;
+            if (MODE == MODE_FULL) done = ring_walk(P, cp, cc, b, zprev, lane, bad, st);
+            if (done) done = traverse<R, MODE>(P, cp, cc, b, lane, bad, st);
 #ifdef SDOT_COUNTERS
             __syncwarp();
             if (lane < 8) atomicAdd(&cp.counters64[lane], (unsigned long long)P.wc[lane]);
@@ -972,7 +1102,7 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
             V3<R> z0;
             z0.x = z0.y = z0.z = R(0);
             float R0 = (float)poly_radius(P, z0, lane);
-            float dpsi = fmaxf(psimax_glob - cp.posf[i].w, 0.f);
+            float dpsi = fmaxf(psimax_glob - cc.si.phi, 0.f);
             if (R0 + sqrtf(R0 * R0 + 2.f * dpsi) > halfLmin * 0.9999f) st |= CS_TOO_LARGE;
         }
         if (!(st & (CS_EMPTY | CS_CAPACITY))) integrate(P, cp, i, lane, bad, st);
@@ -997,12 +1127,28 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
 // per-evaluation preparation: normalised float positions and the psi pyramid
 // ---------------------------------------------------------------------------
 __global__ void posf_kernel(const Pos4* __restrict__ pos, const double* __restrict__ psi,
-                            int64_t N, double inv_a, double inv_a2, float4* __restrict__ posf) {
+                            int64_t N, double inv_a, double inv_a2, double hx, double hy,
+                            double hz, int Gx, int Gy, int Gz, float4* __restrict__ posf,
+                            float* __restrict__ pslo, int32_t* __restrict__ leafc) {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= N) return;
     Pos4 y = pos[s];
-    posf[s] = make_float4((float)(y.x * inv_a), (float)(y.y * inv_a), (float)(y.z * inv_a),
-                          (float)(psi[s] * inv_a2));
+    double h[3] = {hx, hy, hz};
+    int G[3] = {Gx, Gy, Gz};
+    double p[3] = {y.x, y.y, y.z};
+    int c[3];
+    float off[3];
+    for (int a = 0; a < 3; a++) {
+        int cc = (int)floor(p[a] / h[a]);
+        cc = cc < 0 ? 0 : (cc >= G[a] ? G[a] - 1 : cc);
+        c[a] = cc;
+        off[a] = (float)((p[a] - cc * h[a]) * inv_a);
+    }
+    double q = psi[s] * inv_a2;
+    float hi = (float)q;
+    posf[s] = make_float4(off[0], off[1], off[2], hi);
+    pslo[s] = (float)(q - (double)hi);
+    leafc[s] = c[0] | (c[1] << 10) | (c[2] << 20);
 }
 
 __global__ void leaf_max_kernel(const int32_t* __restrict__ cell_start, int64_t ncell,
@@ -1031,18 +1177,22 @@ __global__ void level_max_kernel(const float* __restrict__ in, int dx, int dy, i
 
 int build_pyramid(DeviceState& d, const double* psi, cudaStream_t s) {
     const int64_t N = d.N;
-    posf_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(d.pos, psi, N, 1.0 / d.a,
-                                                          1.0 / (d.a * d.a), d.posf);
+    posf_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(
+        d.pos, psi, N, 1.0 / d.a, 1.0 / (d.a * d.a), d.grid.h[0], d.grid.h[1], d.grid.h[2],
+        d.grid.G[0], d.grid.G[1], d.grid.G[2], d.posf, d.pslo, d.leafc);
+        note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
     Pyramid& P = d.pyr;
     leaf_max_kernel<<<(unsigned)((d.grid.ncell + 255) / 256), 256, 0, s>>>(
         d.grid.cell_start, d.grid.ncell, psi, 1.0 / (d.a * d.a), P.psimax + P.off[0]);
+        note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
     for (int l = 1; l < P.nlev; l++) {
         int64_t n = (int64_t)P.dim[l][0] * P.dim[l][1] * P.dim[l][2];
         level_max_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
             P.psimax + P.off[l - 1], P.dim[l - 1][0], P.dim[l - 1][1], P.dim[l - 1][2],
             P.psimax + P.off[l], P.dim[l][0], P.dim[l][1], P.dim[l][2]);
+            note_launch();
         SDOT_CUDA_TRY(cudaGetLastError());
     }
     return SDOT_OK;
@@ -1137,6 +1287,7 @@ static int launch_clip(const ClipParams& cp, cudaStream_t s) {
     int nb = (int)(need < blocks ? need : blocks);
     if (nb < 1) return SDOT_OK;
     clip_kernel<R, MODE><<<nb, WARPS_PER_BLOCK * 32, smem, s>>>(cp);
+    note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
     return SDOT_OK;
 }
@@ -1161,6 +1312,9 @@ int evaluate_cells(DeviceState& d, const double* psi, int precision, EvalResult*
     }
     cp.pos = d.pos;
     cp.posf = d.posf;
+    cp.pslo = d.pslo;
+    cp.leafc = d.leafc;
+    cp.facets_valid = d.facets_valid;
     cp.psi = psi;
     cp.knn = d.knn;
     cp.knn_d2k = d.knn_d2k;
@@ -1222,8 +1376,10 @@ int evaluate_cells(DeviceState& d, const double* psi, int precision, EvalResult*
     }
     cudaEventRecord(e1, s);
     cell_reduce_kernel<<<RED_BLOCKS, 256, 0, s>>>(d.vol, d.nu, d.status, d.N, d.partials);
+    note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
     cell_reduce_final<<<1, 32, 0, s>>>(d.partials, RED_BLOCKS, d.scal);
+    note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
     double h[6];
     SDOT_CUDA_TRY(cudaMemcpyAsync(h, d.scal, sizeof h, cudaMemcpyDeviceToHost, s));
@@ -1238,6 +1394,7 @@ int evaluate_cells(DeviceState& d, const double* psi, int precision, EvalResult*
     cudaEventDestroy(e1);
     cudaEventDestroy(ep1);
     cudaEventDestroy(ep2);
+    d.facets_valid = 1;  // every cell now holds its facets of this diagram
     res->sum_vol = h[0];
     res->max_rel_err = h[1];
     res->l2_err = h[2];

@@ -19,6 +19,10 @@
 
 namespace sdot {
 
+static unsigned long long g_launches = 0;
+void note_launch() { __atomic_add_fetch(&g_launches, 1ull, __ATOMIC_RELAXED); }
+unsigned long long launch_count() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
 int num_sms() {
     static int n = 0;
     if (n == 0) {
@@ -119,16 +123,19 @@ static int scan_impl(const Tin* in, Tout* out, int64_t n, char* temp, cudaStream
     int64_t nb = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
     if (nb == 1) {
         scan_apply_kernel<Tin, Tout><<<1, SCAN_THREADS, 0, s>>>(in, out, n, nullptr);
+        note_launch();
         SDOT_CUDA_TRY(cudaGetLastError());
         return SDOT_OK;
     }
     Tout* sums = reinterpret_cast<Tout*>(temp);
     char* next = temp + ((nb * sizeof(Tout) + 255) / 256) * 256;
     scan_sums_kernel<Tin, Tout><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, sums);
+    note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
     int rc = scan_impl<Tout, Tout>(sums, sums, nb, next, s);
     if (rc) return rc;
     scan_apply_kernel<Tin, Tout><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, n, sums);
+    note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
     return SDOT_OK;
 }
@@ -248,6 +255,7 @@ int build_grid(DeviceState& d, const double* pos_user_dev, double seeds_per_leaf
     SDOT_CUDA_TRY(cudaMemsetAsync(bad, 0, 4, s));
     unsigned nb = (unsigned)((N + 255) / 256);
     keys_kernel<<<nb, 256, 0, s>>>(pos_user_dev, N, gp, key, count, bad);
+    note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
     // cell_start = exclusive scan of counts, with cell_start[ncell] = N
     int rc = scan_exclusive_i32(count, d.grid.cell_start, ncell, t, s);
@@ -255,11 +263,14 @@ int build_grid(DeviceState& d, const double* pos_user_dev, double seeds_per_leaf
     int32_t nN = (int32_t)N;
     SDOT_CUDA_TRY(cudaMemcpyAsync(d.grid.cell_start + ncell, &nN, 4, cudaMemcpyHostToDevice, s));
     scatter_kernel<<<nb, 256, 0, s>>>(key, N, d.grid.cell_start, fill, d.perm);
+    note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
     sort_cells_kernel<<<(unsigned)((ncell + 255) / 256), 256, 0, s>>>(d.grid.cell_start, ncell,
                                                                      d.perm);
+                                                                     note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
     finalize_sort_kernel<<<nb, 256, 0, s>>>(pos_user_dev, N, d.perm, d.iperm, d.pos);
+    note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
     int hbad = 0;
     SDOT_CUDA_TRY(cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, s));
@@ -432,6 +443,7 @@ int build_knn(DeviceState& d, cudaStream_t s, int* dup_flag_host) {
         knn_kernel<48><<<nb, 128, 0, s>>>(d.pos, d.grid.cell_start, p, d.knn, d.knn_d2k, flags);
     else
         knn_kernel<64><<<nb, 128, 0, s>>>(d.pos, d.grid.cell_start, p, d.knn, d.knn_d2k, flags);
+    note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
     int h = 0;
     SDOT_CUDA_TRY(cudaMemcpyAsync(&h, flags, 4, cudaMemcpyDeviceToHost, s));
@@ -452,6 +464,7 @@ __global__ void knn_user_kernel(const int32_t* __restrict__ knn, const int32_t* 
 int knn_to_user(const DeviceState& d, int32_t* out, cudaStream_t s) {
     int64_t n = d.N * d.k;
     knn_user_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d.knn, d.perm, d.N, d.k, out);
+    note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
     return SDOT_OK;
 }

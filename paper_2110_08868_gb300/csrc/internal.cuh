@@ -73,7 +73,10 @@ struct DeviceState {
     double a;                 // length unit: (|box| / N)^(1/3)
     // seeds
     Pos4* pos;             // sorted positions; w = caller index (exact in fp64)
-    float4* posf;             // (x/a, y/a, z/a, psi/a^2), refreshed per evaluation
+    float4* posf;             // (offset in grid cell / a, psi/a^2 hi), per evaluation
+    float* pslo;              // psi/a^2 lo part (psi/a^2 = hi + lo)
+    int32_t* leafc;           // grid cell of each seed: x | y << 10 | z << 20
+    int facets_valid;         // fcnt/fcol hold a complete previous diagram
     int32_t* perm;            // sorted -> caller index
     int32_t* iperm;           // caller -> sorted index
     double* nu;               // masses (sorted)
@@ -130,6 +133,10 @@ void set_error(const std::string& msg);
 // launchers (host functions defined in the .cu files)
 // ---------------------------------------------------------------------------
 int num_sms();
+
+// process-wide count of kernel launches issued by this library
+void note_launch();
+unsigned long long launch_count();
 
 // exclusive scans (in may alias out); temp must hold scan_temp_elems(n) elements
 size_t scan_temp_bytes(int64_t n);

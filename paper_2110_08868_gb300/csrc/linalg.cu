@@ -79,6 +79,7 @@ int csr_count(DeviceState& d, int64_t* nnz_out, cudaStream_t s) {
     const int64_t N = d.N;
     unsigned nb = (unsigned)((N + 255) / 256);
     csr_count_kernel<<<nb, 256, 0, s>>>(d.fcnt, d.fcol, d.fval, N, d.rowcnt);
+    note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
     // row_ptr = exclusive scan over N+1 entries (rowcnt[N] == 0)
     SDOT_CUDA_TRY(cudaMemsetAsync(d.rowcnt + N, 0, 4, s));
@@ -95,6 +96,7 @@ int csr_fill(DeviceState& d, cudaStream_t s) {
     const int64_t N = d.N;
     unsigned nb = (unsigned)((N + 255) / 256);
     csr_fill_kernel<<<nb, 256, 0, s>>>(d.fcnt, d.fcol, d.fval, N, d.row_ptr, d.col, d.val, d.dinv);
+    note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
     return SDOT_OK;
 }
@@ -138,12 +140,14 @@ int assemble_csr_user(DeviceState& d, int64_t nnz, cudaStream_t s) {
     const int64_t N = d.N;
     unsigned nb = (unsigned)((N + 255) / 256);
     csr_user_count<<<nb, 256, 0, s>>>(d.row_ptr, d.perm, N, d.rowcnt);
+    note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
     SDOT_CUDA_TRY(cudaMemsetAsync(d.rowcnt + N, 0, 4, s));
     int rc = scan_exclusive_i32_to_i64(d.rowcnt, d.row_ptr_u, N + 1, d.partials + 4096, s);
     if (rc) return rc;
     csr_user_fill<<<nb, 256, 0, s>>>(d.row_ptr, d.col, d.val, d.perm, N, d.row_ptr_u, d.col_u,
                                      d.val_u);
+                                     note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
     return SDOT_OK;
 }
@@ -299,9 +303,11 @@ int pcg_solve(DeviceState& d, double rtol, int maxit, int* iters, double* rel_re
     double mean = (box - sums[0]) / (double)N;
     pcg_init_kernel<<<nb, PCG_THREADS, 0, s>>>(d.nu, d.vol, mean, d.dinv, N, d.x, d.r, d.z, d.p,
                                                partB[1]);
+                                               note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
     double h[2];
     partial_final_kernel<<<1, PCG_THREADS, 0, s>>>(partB[1], nb, 2, 1, hs);
+    note_launch();
     SDOT_CUDA_TRY(cudaMemcpyAsync(h, hs, 8, cudaMemcpyDeviceToHost, s));
     SDOT_CUDA_TRY(cudaStreamSynchronize(s));
     const double rr0 = h[0];
@@ -317,12 +323,16 @@ int pcg_solve(DeviceState& d, double rtol, int maxit, int* iters, double* rel_re
             double* prev = partB[(it + 1) & 1];
             double* cur = partB[it & 1];
             pcg_spmv_kernel<<<nb, PCG_THREADS, 0, s>>>(d.row_ptr, d.col, d.val, d.p, N, d.q, partA);
+            note_launch();
             pcg_update_kernel<<<nb, PCG_THREADS, 0, s>>>(partA, prev, cur, nb, d.dinv, N, d.x, d.r,
                                                          d.z, d.p, d.q);
+                                                         note_launch();
             pcg_dir_kernel<<<nb, PCG_THREADS, 0, s>>>(prev, cur, nb, N, d.z, d.p);
+            note_launch();
         }
         SDOT_CUDA_TRY(cudaGetLastError());
         partial_final_kernel<<<1, PCG_THREADS, 0, s>>>(partB[(it - 1) & 1], nb, 2, 1, hs);
+        note_launch();
         SDOT_CUDA_TRY(cudaMemcpyAsync(h, hs, 8, cudaMemcpyDeviceToHost, s));
         SDOT_CUDA_TRY(cudaStreamSynchronize(s));
         rr = h[0];
@@ -345,6 +355,7 @@ __global__ void axpy_kernel(const double* __restrict__ a, const double* __restri
 int axpy_gauge(DeviceState& d, const double* psi, const double* delta, double alpha, double* out,
                cudaStream_t s) {
     axpy_kernel<<<(unsigned)((d.N + 255) / 256), 256, 0, s>>>(psi, delta, alpha, d.N, out);
+    note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
     return SDOT_OK;
 }
@@ -371,7 +382,9 @@ __global__ void sub_mean_kernel(double* __restrict__ v, int64_t N, const double*
 int subtract_mean(DeviceState& d, double* v, cudaStream_t s) {
     const int nb = 2 * num_sms();
     sum_kernel<<<nb, 256, 0, s>>>(v, d.N, d.partials);
+    note_launch();
     sub_mean_kernel<<<nb, 256, 0, s>>>(v, d.N, d.partials, nb);
+    note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
     return SDOT_OK;
 }
@@ -398,6 +411,7 @@ int scatter_to_user(const DeviceState& d, const double* sorted, double* user, in
                     cudaStream_t s) {
     int64_t n = d.N * w;
     scatter_kernel_w<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sorted, d.perm, d.N, w, user);
+    note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
     return SDOT_OK;
 }
@@ -406,6 +420,7 @@ int gather_from_user(const DeviceState& d, const double* user, double* sorted, i
                      cudaStream_t s) {
     int64_t n = d.N * w;
     gather_kernel_w<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(user, d.perm, d.N, w, sorted);
+    note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
     return SDOT_OK;
 }
@@ -450,6 +465,7 @@ __global__ void status_kernel(const uint8_t* __restrict__ st, const int32_t* __r
 
 int status_to_user(const DeviceState& d, uint8_t* out, cudaStream_t s) {
     status_kernel<<<(unsigned)((d.N + 255) / 256), 256, 0, s>>>(d.status, d.perm, d.N, out);
+    note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
     return SDOT_OK;
 }
@@ -457,6 +473,7 @@ int status_to_user(const DeviceState& d, uint8_t* out, cudaStream_t s) {
 int centroids_user(const DeviceState& d, double* out, int wrap_abs, cudaStream_t s) {
     centroid_kernel<<<(unsigned)((d.N + 255) / 256), 256, 0, s>>>(
         d.pos, d.m1, d.vol, d.perm, d.N, d.L[0], d.L[1], d.L[2], wrap_abs, out);
+        note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
     return SDOT_OK;
 }
@@ -487,6 +504,7 @@ __global__ void mass_kernel(const double* __restrict__ nu, int64_t N, double* __
 int check_masses(const DeviceState& d, double* sum_out, double* min_out, cudaStream_t s) {
     const int nb = 64;
     mass_kernel<<<nb, 256, 0, s>>>(d.nu, d.N, d.partials);
+    note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
     double h[2 * nb];
     SDOT_CUDA_TRY(cudaMemcpyAsync(h, d.partials, sizeof h, cudaMemcpyDeviceToHost, s));
