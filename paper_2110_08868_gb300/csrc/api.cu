@@ -344,6 +344,9 @@ int sdot_create(const double* pos, const double* mass, int64_t N, const double b
     }
     if (cudaMemsetAsync(d.psi, 0, (size_t)N * 8, s) != cudaSuccess ||
         cudaMemsetAsync(d.anchor, 0, (size_t)N * 12, s) != cudaSuccess ||
+        cudaMemsetAsync(d.fcnt, 0, (size_t)N * 4, s) != cudaSuccess ||
+        cudaMemsetAsync(d.fcol, 0, (size_t)N * FCAP * 4, s) != cudaSuccess ||
+        cudaMemsetAsync(d.fval, 0, (size_t)N * FCAP * 8, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
         set_error("sdot_create: initialisation failed");
         return fail(SDOT_ERR_CUDA);
@@ -468,6 +471,23 @@ int sdot_solve(sdot_ctx* c, double tol, const double* psi0, sdot_stats* st) {
         cudaEventElapsedTime(&ms, c0, c1);
         S.ms_cg += ms;
         S.cg_iters += cg_it;
+        if (c->opt.verbose > 1) {
+            std::vector<double> h((size_t)d.N), dg((size_t)d.N);
+            cudaMemcpy(h.data(), d.x, (size_t)d.N * 8, cudaMemcpyDeviceToHost);
+            cudaMemcpy(dg.data(), d.dinv, (size_t)d.N * 8, cudaMemcpyDeviceToHost);
+            double mx = 0, mn = 0;
+            int64_t nonfinite = 0, zero_dinv = 0;
+            for (int64_t t = 0; t < d.N; t++) {
+                if (!isfinite(h[t])) nonfinite++;
+                else { mx = fmax(mx, h[t]); mn = fmin(mn, h[t]); }
+                if (dg[t] == 0.0) zero_dinv++;
+            }
+            fprintf(stderr,
+                    "{\"pcg_iters\": %d, \"pcg_rel_res\": %.3e, \"nnz\": %lld, \"delta_min\": %.3e, "
+                    "\"delta_max\": %.3e, \"nonfinite\": %lld, \"zero_diag\": %lld}\n",
+                    cg_it, cg_res, (long long)c->nnz, mn, mx, (long long)nonfinite,
+                    (long long)zero_dinv);
+        }
         alpha = 1.0;
         int trials = 0;
         EvalResult et;
@@ -479,6 +499,13 @@ int sdot_solve(sdot_ctx* c, double tol, const double* psi0, sdot_stats* st) {
             S.ms_clip += et.ms;
             for (int q = 0; q < 3; q++) S.ms_pass[q] += et.ms_pass[q];
             bool valid = !(et.flags & (CS_TOO_LARGE | CS_CAPACITY));
+            if (c->opt.verbose > 1)
+                fprintf(stderr,
+                        "{\"trial_alpha\": %g, \"flags\": %u, \"min_vol\": %.6e, \"l2_err\": %.6e, "
+                        "\"target\": %.6e, \"sum_vol_rel\": %.3e, \"requeued\": %lld, \"reclipped\": %lld}\n",
+                        alpha, et.flags, et.min_vol, et.l2_err, (1.0 - 0.5 * alpha) * ev.l2_err,
+                        et.sum_vol / (d.L[0] * d.L[1] * d.L[2]) - 1.0, (long long)et.requeued,
+                        (long long)et.reclipped);
             if (valid && et.min_vol >= eps0 && et.l2_err <= (1.0 - 0.5 * alpha) * ev.l2_err) break;
             alpha *= 0.5;
             if (alpha < c->opt.alpha_min) {

@@ -60,7 +60,9 @@ struct WarpPoly {
     uint32_t wc[8];         // work counters of the current cell (diagnostic builds)
 };
 
-// Work counters, compiled in only with -DSDOT_COUNTERS (diagnostic builds):
+// Work counters, compiled in only with -DSDOT_COUNTERS (diagnostic builds). The
+// count argument is evaluated by lane 0 only, so it must not contain a warp vote:
+// take votes before the macro.
 // 0 clip calls, 1 cuts, 2 node tests, 3 leaf visits, 4 seed tests, 5 candidates,
 // 6 cells, 7 pyramid-walk rounds
 #ifdef SDOT_COUNTERS
@@ -722,7 +724,12 @@ __device__ __noinline__ int process_leaves(WarpPoly<R>& P, const ClipParams& cp,
     int n = se - sb;
     int maxn = n;
     for (int o = 16; o > 0; o >>= 1) maxn = max(maxn, __shfl_xor_sync(FULLMASK, maxn, o));
-    WCOUNT(P, 3, __popc(__ballot_sync(FULLMASK, leaf >= 0)));
+#ifdef SDOT_COUNTERS
+    {
+        const uint32_t nleaf = __popc(__ballot_sync(FULLMASK, leaf >= 0));
+        WCOUNT(P, 3, nleaf);
+    }
+#endif
     for (int u = 0; u < maxn; u++) {
         int32_t s = sb + u;
         bool cand = false;
@@ -731,7 +738,12 @@ __device__ __noinline__ int process_leaves(WarpPoly<R>& P, const ClipParams& cp,
             plane_f32(cp, cc.si, s, nx, ny, nz, w);
             cand = box_may_cut(b, nx, ny, nz, w);
         }
-        WCOUNT(P, 4, __popc(__ballot_sync(FULLMASK, u < n)));
+#ifdef SDOT_COUNTERS
+        {
+            const uint32_t nseed = __popc(__ballot_sync(FULLMASK, u < n));
+            WCOUNT(P, 4, nseed);
+        }
+#endif
         uint32_t cm = __ballot_sync(FULLMASK, cand);
         WCOUNT(P, 5, __popc(cm));
         while (cm) {
@@ -1005,7 +1017,8 @@ __device__ int clip_list(WarpPoly<R>& P, const ClipParams& cp, const CellCtx& cc
         int32_t j = -1;
         if (t < n) {
             j = list[t];
-            build_plane(cp, cc, j, pl, len);
+            if (j >= 0 && j < cp.N && j != (int32_t)cc.i) build_plane(cp, cc, j, pl, len);
+            else j = -1;  // out-of-range entry: a no-op plane far outside
         }
         int nk = min(32, n - t0);
         for (int u = 0; u < nk; u++) {
@@ -1016,6 +1029,13 @@ __device__ int clip_list(WarpPoly<R>& P, const ClipParams& cp, const CellCtx& cc
             pn.w = __shfl_sync(FULLMASK, pl.w, u);
             R plen = __shfl_sync(FULLMASK, len, u);
             int32_t ju = __shfl_sync(FULLMASK, j, u);
+            if (ju < 0) continue;
+            // a seed already among the planes (the lists overlap) is not applied twice
+            bool dup = false;
+#pragma unroll
+            for (int w = 0; w < MAXP / 32; w++)
+                dup |= (lane + 32 * w < P.np && P.pj[lane + 32 * w] == ju);
+            if (__any_sync(FULLMASK, dup)) continue;
             int rc = poly_clip(P, pn, plen, ju, lane, bad);
             if (rc == CLIP_EMPTY || rc == CLIP_CAP) return rc;
         }
@@ -1062,7 +1082,11 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
         // first candidates: the cell's facets in the previous diagram, then its k
         // nearest seeds
         int rc = CLIP_NONE;
+#ifdef SDOT_DIAG_NO_PREV
+        if (false) {
+#else
         if (cp.facets_valid) {
+#endif
             int nprev = min(cp.fcnt[i], FCAP);
             rc = clip_list(P, cp, cc, cp.fcol + i * FCAP, nprev, lane, bad);
         }
@@ -1108,10 +1132,14 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
         if (!(st & (CS_EMPTY | CS_CAPACITY))) integrate(P, cp, i, lane, bad, st);
         if (bad) st |= CS_INCONSISTENT;
         if (lane == 0) {
+            if (st & (CS_EMPTY | CS_CAPACITY)) {
+                // no facets from this cell (an empty cell has none; a cell over capacity
+                // is re-clipped or reported, and must not leave stale facet counts)
+                cp.fcnt[i] = 0;
+            }
             if (st & CS_EMPTY) {
                 cp.vol[i] = 0.0;
                 cp.m1[3 * i] = cp.m1[3 * i + 1] = cp.m1[3 * i + 2] = 0.0;
-                cp.fcnt[i] = 0;
             }
             cp.status[i] = (uint8_t)st;
             bool redo = sizeof(R) == 4 && (st & (CS_INCONSISTENT | CS_CAPACITY));

@@ -22,15 +22,30 @@ namespace sdot {
 // ---------------------------------------------------------------------------
 // CSR assembly
 // ---------------------------------------------------------------------------
+// Symmetrised coefficient of facet t of cell i, or 0 when it must not enter the
+// matrix: the first occurrence of column j in row i carries the whole pair
+// 1/2 (sum of cell i's reports of j + sum of cell j's reports of i); later duplicate
+// occurrences and facets reported by one side only give 0. L is therefore exactly
+// symmetric even when a cell reports a neighbour twice.
 __device__ __forceinline__ double sym_value(const int32_t* __restrict__ fcnt,
                                             const int32_t* __restrict__ fcol,
                                             const double* __restrict__ fval, int64_t i, int t) {
-    int32_t j = fcol[i * FCAP + t];
-    double c = fval[i * FCAP + t];
-    int n = fcnt[j];
-    for (int u = 0; u < n; u++)
-        if (fcol[(int64_t)j * FCAP + u] == (int32_t)i) return 0.5 * (c + fval[(int64_t)j * FCAP + u]);
-    return 0.0;
+    const int32_t j = fcol[i * FCAP + t];
+    for (int u = 0; u < t; u++)
+        if (fcol[i * FCAP + u] == j) return 0.0;  // not the first occurrence
+    double cij = 0.0;
+    const int ni = fcnt[i];
+    for (int u = t; u < ni; u++)
+        if (fcol[i * FCAP + u] == j) cij += fval[i * FCAP + u];
+    double cji = 0.0;
+    bool seen = false;
+    const int nj = fcnt[j];
+    for (int u = 0; u < nj; u++)
+        if (fcol[(int64_t)j * FCAP + u] == (int32_t)i) {
+            cji += fval[(int64_t)j * FCAP + u];
+            seen = true;
+        }
+    return seen ? 0.5 * (cij + cji) : 0.0;
 }
 
 __global__ void csr_count_kernel(const int32_t* __restrict__ fcnt, const int32_t* __restrict__ fcol,

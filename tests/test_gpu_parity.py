@@ -5,7 +5,9 @@ Tolerances (from the arithmetic, stated here once):
   * FP64 volumes / centroids: 1e-10 relative (to a^3 / a); Hessian entries 1e-10 of the
     row diagonal.
   * Mixed precision (FP32 geometry in units of the spacing a, FP64 sums): volumes 2e-5
-    relative, centroids 2e-5 a, Hessian 2e-4 of the diagonal; the solve reaches the same
+    relative, centroids 2e-5 a; Hessian entries 1e-3 of the row diagonal (FP32 may
+    resolve a facet of area below ~1e-3 a^2 differently on the two sides, and the
+    assembly drops facets one side does not report); the solve reaches the same
     max|V - nu|/nu criterion.
   * Displacement at convergence (both sides solved to 1e-10): 1e-6 a.
 """
@@ -58,7 +60,7 @@ def test_knn_bit_exact_ties_and_ragged(k):
 
 
 @pytest.mark.parametrize("prec,vtol,ctol,htol", [("fp64", 1e-10, 1e-10, 1e-10),
-                                                  ("mixed", 2e-5, 2e-5, 2e-4)])
+                                                  ("mixed", 2e-5, 2e-5, 1e-3)])
 def test_laguerre_psi0_c1(prec, vtol, ctol, htol):
     y, nu, L = c1()
     N = y.shape[0]
@@ -74,7 +76,7 @@ def test_laguerre_psi0_c1(prec, vtol, ctol, htol):
     assert ok, err
 
 
-@pytest.mark.parametrize("prec,vtol,htol", [("fp64", 1e-10, 1e-10), ("mixed", 2e-5, 2e-4)])
+@pytest.mark.parametrize("prec,vtol,htol", [("fp64", 1e-10, 1e-10), ("mixed", 2e-5, 1e-3)])
 def test_laguerre_random_psi_c1(prec, vtol, htol):
     # a non-trivial psi (the oracle's Newton direction after one step) makes the
     # cells leave their seeds, which exercises the security test and the re-queue
@@ -89,6 +91,25 @@ def test_laguerre_random_psi_c1(prec, vtol, htol):
     np.testing.assert_allclose(g["vol"], o["vol"], rtol=0, atol=vtol * a ** 3)
     ok, err = _hess_close(g["hess"], o["L"], htol)
     assert ok, err
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_hessian_exactly_symmetric_zero_rowsum(prec):
+    # after a few warm-started evaluations at moving psi (the solve's access pattern)
+    y, nu, L = c1()
+    N = y.shape[0]
+    a = L / 16
+    s = B.Solver(y, [L] * 3, precision=prec)
+    rng = np.random.default_rng(3)
+    for step in range(4):
+        g = s.laguerre(0.05 * step * a * a * rng.standard_normal(N), with_hessian=True,
+                       allow_empty=True)
+        H = g["hess"]
+        assert abs(H - H.T).max() == 0.0
+        assert np.abs(np.asarray(H.sum(axis=1))).max() <= 1e-12 * H.diagonal().max()
+        assert (H.diagonal() >= 0).all()
+        off = H - __import__("scipy.sparse", fromlist=["diags"]).diags(H.diagonal())
+        assert off.max() <= 0.0
 
 
 def test_solve_fp64_matches_oracle_displacement():
