@@ -602,10 +602,23 @@ __device__ void poly_bounds(const WarpPoly<R>& P, const ClipParams& cp, Bounds& 
     }
 }
 
-// true when every seed of node (level l, coordinates X, Y, Z) provably cannot cut:
-// for a seed j in the node, c.d + Rc |d| <= 1/2|d|^2 + psi_i - psi_j follows from
-// 1/2 u^2 - 1/2|c|^2 - Rc dmax - (psimax - psi_i) >= 0 with u the distance from the
-// anchor c to the node and dmax the largest distance from the seed to the node.
+// min over d in [l, h] of f(d) = 1/2 d^2 - max(d bmax, d bmin) (a piecewise parabola
+// with its minima at d = bmax >= 0 and d = bmin <= 0)
+__device__ __forceinline__ float fmin_axis(float l, float h, float bmn, float bmx) {
+    float fl = 0.5f * l * l - (l >= 0.f ? l * bmx : l * bmn);
+    float fh = 0.5f * h * h - (h >= 0.f ? h * bmx : h * bmn);
+    float m = fminf(fl, fh);
+    if (bmx > 0.f && l < bmx && bmx < h) m = fminf(m, -0.5f * bmx * bmx);
+    if (bmn < 0.f && l < bmn && bmn < h) m = fminf(m, -0.5f * bmn * bmn);
+    return m;
+}
+
+// True when no seed of node (level l, coordinates X, Y, Z) can cut the polytope. For a
+// seed j with d = its minimum-image offset, max_vertex v.d <= S(d) = sum_a max(d_a bmax_a,
+// d_a bmin_a) (support of the bounding box), so j cannot cut when
+//     sum_a [1/2 d_a^2 - max(d_a bmax_a, d_a bmin_a)] >= psi_j - psi_i.
+// Each term is minimised over the node's offset interval on its axis, psi_j is bounded
+// by the node's psimax.
 __device__ __forceinline__ bool node_pruned(const ClipParams& cp, const Bounds& b, int l, int X,
                                             int Y, int Z) {
     float pm = cp.pyr.psimax[cp.pyr.off[l] +
@@ -613,21 +626,32 @@ __device__ __forceinline__ bool node_pruned(const ClipParams& cp, const Bounds& 
     if (pm == -INFINITY) return true;  // no seed inside
     int span = 1 << (2 * l);
     int c[3] = {X, Y, Z};
-    float u2 = 0.f, dm2 = 0.f;
+    float val = 0.f, mag = 0.f;
 #pragma unroll
     for (int a = 0; a < 3; a++) {
         int c0 = c[a] * span, c1 = min((c[a] + 1) * span, cp.G[a]);
         float lo = c0 * cp.ht[a], hi = (c1 == cp.G[a]) ? cp.Lt[a] : c1 * cp.ht[a];
-        float g = circ_gap(b.cabs[a], lo, hi, cp.Lt[a]);
-        float f = circ_far(b.yabs[a], lo, hi, cp.Lt[a]);
-        u2 += g * g;
-        dm2 += f * f;
+        const float Lt = cp.Lt[a], hL = cp.halfLt[a];
+        float w = hi - lo;
+        float m;
+        if (w >= Lt) {
+            m = fmin_axis(-hL, hL, b.bmin[a], b.bmax[a]);
+        } else {
+            float o = lo - b.yabs[a];  // offset of the node start, minimum image
+            o -= Lt * floorf((o + hL) / Lt);
+            if (o + w <= hL) {
+                m = fmin_axis(o, o + w, b.bmin[a], b.bmax[a]);
+            } else {  // the interval wraps through +-L/2
+                m = fminf(fmin_axis(o, hL, b.bmin[a], b.bmax[a]),
+                          fmin_axis(-hL, o + w - Lt, b.bmin[a], b.bmax[a]));
+            }
+        }
+        val += m;
+        mag += fabsf(m);
     }
-    float dmax = sqrtf(dm2);
-    float t1 = 0.5f * u2, t2 = b.Rc * dmax, dpsi = pm - b.psi_i;
-    float val = t1 - b.c2h - t2 - dpsi;
-    float margin = 2e-5f * (t1 + b.c2h + t2 + fabsf(pm) + fabsf(b.psi_i)) + 1e-5f;
-    return val > margin;
+    float dpsi = pm - b.psi_i;
+    float margin = 2e-5f * (mag + fabsf(pm) + fabsf(b.psi_i)) + 1e-5f;
+    return val - dpsi > margin;
 }
 
 // conservative FP32 test: can the plane (n, w) reach the polytope's bounding box?
