@@ -57,12 +57,13 @@ typedef struct {
     int k;                 /* neighbours per seed in the kNN list (1..64, default 24) */
     int precision;         /* SDOT_PREC_FP64 or SDOT_PREC_MIXED (default MIXED) */
     double seeds_per_leaf; /* mean seeds per grid cell of the spatial hash (default 2) */
-    double cg_rtol;        /* PCG stop: ||r|| <= cg_rtol ||g|| (default 1e-3; tightened
-                              near convergence to 0.1 tol) */
+    double cg_rtol;        /* PCG stop: ||r|| <= cg_rtol ||g|| (default 1e-3) */
     int cg_maxit;          /* PCG iteration cap per Newton step (default 5000) */
     int newton_maxit;      /* Newton iteration cap (default 100) */
     double alpha_min;      /* smallest damping step before SDOT_ERR_NO_DESCENT (2^-30) */
     int verbose;           /* 1: one JSON line per Newton iteration on stderr */
+    int warm_alpha;        /* 1 (default): each line search starts at min(1, 4 alpha_prev)
+                              instead of 1; 0: always 1, 1/2, 1/4, ... */
 } sdot_options;
 
 /* The Hessian in CSR form. L = -Hessian(K) is the weighted graph Laplacian
@@ -134,9 +135,10 @@ int sdot_laguerre(sdot_ctx* ctx, const double* psi, double* volumes, double* cen
  * Damped Newton maximisation of K (concave and C^2, Sec. "Monge-Ampere-Kantorovich
  * Reconstruction") from psi0 (N doubles; NULL: 0) until
  * max_j |V_j - nu_j| / nu_j <= tol. Each step solves L delta = nu - V by
- * Jacobi-preconditioned CG and takes the first alpha in 1, 1/2, 1/4, ... with
+ * Jacobi-preconditioned CG and takes the first alpha in a0, a0/2, a0/4, ... with
  * min_j V_j >= eps0 and ||nu - V||_2 <= (1 - alpha/2) ||nu - V(psi)||_2, where
- * eps0 = 1/2 min(min_j V_j(psi0), min_j nu_j). The result keeps sum(psi) = 0.
+ * eps0 = 1/2 min(min_j V_j(psi0), min_j nu_j); a0 = 1, or min(1, 4 alpha_prev) after
+ * the first step when opt.warm_alpha is set. The result keeps sum(psi) = 0.
  * st may be NULL.
  */
 int sdot_solve(sdot_ctx* ctx, double tol, const double* psi0, sdot_stats* st);

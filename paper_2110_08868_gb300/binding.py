@@ -32,7 +32,8 @@ class sdot_options(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("precision", ctypes.c_int),
                 ("seeds_per_leaf", ctypes.c_double), ("cg_rtol", ctypes.c_double),
                 ("cg_maxit", ctypes.c_int), ("newton_maxit", ctypes.c_int),
-                ("alpha_min", ctypes.c_double), ("verbose", ctypes.c_int)]
+                ("alpha_min", ctypes.c_double), ("verbose", ctypes.c_int),
+                ("warm_alpha", ctypes.c_int)]
 
 
 class sdot_csr(ctypes.Structure):

@@ -182,6 +182,7 @@ int sdot_default_options(sdot_options* o) {
     o->newton_maxit = 100;
     o->alpha_min = 1.0 / (1 << 30);
     o->verbose = 0;
+    o->warm_alpha = 1;
     return SDOT_OK;
 }
 
@@ -488,7 +489,10 @@ int sdot_solve(sdot_ctx* c, double tol, const double* psi0, sdot_stats* st) {
                     cg_it, cg_res, (long long)c->nnz, mn, mx, (long long)nonfinite,
                     (long long)zero_dinv);
         }
-        alpha = 1.0;
+        // damping: alpha = 1, 1/2, 1/4, ... (first acceptable); with alpha_warm the
+        // sequence starts at min(1, 4 alpha_prev) instead of 1
+        alpha = c->opt.warm_alpha ? fmin(1.0, 4.0 * alpha) : 1.0;
+        if (it == 0) alpha = 1.0;
         int trials = 0;
         EvalResult et;
         while (true) {

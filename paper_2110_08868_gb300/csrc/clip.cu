@@ -297,8 +297,8 @@ __device__ __forceinline__ bool beyond(const V3<R>& v, const V4<R>& pn, R plen, 
 
 // Clip by p.n <= w (tag j). Non-finite geometry sets bad.
 template <typename R>
-__device__ __noinline__ int poly_clip(WarpPoly<R>& P, const V4<R>& pn, R plen, int32_t j, int lane,
-                         bool& bad) {
+__device__ __forceinline__ int poly_clip_inl(WarpPoly<R>& P, const V4<R>& pn, R plen, int32_t j,
+                                             int lane, bool& bad) {
     constexpr int SL = MAXT / 32;  // vertex slots per lane
     const int nt = P.nt;
     bool out[SL];
@@ -456,6 +456,12 @@ __device__ __noinline__ int poly_clip(WarpPoly<R>& P, const V4<R>& pn, R plen, i
     if (__any_sync(FULLMASK, lbad)) bad = true;
     __syncwarp();
     return CLIP_CUT;
+}
+
+template <typename R>
+__device__ __noinline__ int poly_clip(WarpPoly<R>& P, const V4<R>& pn, R plen, int32_t j, int lane,
+                                      bool& bad) {
+    return poly_clip_inl(P, pn, plen, j, lane, bad);
 }
 
 template <typename R>
@@ -651,7 +657,24 @@ __device__ __forceinline__ bool node_pruned(const ClipParams& cp, const Bounds& 
     }
     float dpsi = pm - b.psi_i;
     float margin = 2e-5f * (mag + fabsf(pm) + fabsf(b.psi_i)) + 1e-5f;
-    return val - dpsi > margin;
+    if (val - dpsi > margin) return true;
+    // second valid bound, better in diagonal directions: every vertex lies within Rc
+    // of the box centre c, so max_v v.d <= c.d + Rc |d|, and 1/2|d|^2 - c.d =
+    // 1/2|d - c|^2 - 1/2|c|^2 with |d - c| >= u (anchor-to-node distance), |d| <= dmax
+    float u2 = 0.f, dm2 = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        int c0 = c[a] * span, c1 = min((c[a] + 1) * span, cp.G[a]);
+        float lo = c0 * cp.ht[a], hi = (c1 == cp.G[a]) ? cp.Lt[a] : c1 * cp.ht[a];
+        float g = circ_gap(b.cabs[a], lo, hi, cp.Lt[a]);
+        float f = circ_far(b.yabs[a], lo, hi, cp.Lt[a]);
+        u2 += g * g;
+        dm2 += f * f;
+    }
+    float t1 = 0.5f * u2, t2 = b.Rc * sqrtf(dm2);
+    float val2 = t1 - b.c2h - t2 - dpsi;
+    float margin2 = 2e-5f * (t1 + b.c2h + t2 + fabsf(pm) + fabsf(b.psi_i)) + 1e-5f;
+    return val2 > margin2;
 }
 
 // conservative FP32 test: can the plane (n, w) reach the polytope's bounding box?
@@ -1031,8 +1054,8 @@ __device__ __noinline__ void integrate(WarpPoly<R>& P, const ClipParams& cp, int
 // clip by a list of seeds (warp-uniform count): each lane builds one plane, then the
 // warp clips by them in order
 template <typename R>
-__device__ int clip_list(WarpPoly<R>& P, const ClipParams& cp, const CellCtx& cc,
-                         const int32_t* list, int n, int lane, bool& bad) {
+__device__ __noinline__ int clip_list(WarpPoly<R>& P, const ClipParams& cp, const CellCtx& cc,
+                                      const int32_t* list, int n, int lane, bool& bad) {
     for (int t0 = 0; t0 < n; t0 += 32) {
         int t = t0 + lane;
         V4<R> pl;
@@ -1060,7 +1083,7 @@ __device__ int clip_list(WarpPoly<R>& P, const ClipParams& cp, const CellCtx& cc
             for (int w = 0; w < MAXP / 32; w++)
                 dup |= (lane + 32 * w < P.np && P.pj[lane + 32 * w] == ju);
             if (__any_sync(FULLMASK, dup)) continue;
-            int rc = poly_clip(P, pn, plen, ju, lane, bad);
+            int rc = poly_clip_inl(P, pn, plen, ju, lane, bad);
             if (rc == CLIP_EMPTY || rc == CLIP_CAP) return rc;
         }
     }
@@ -1068,7 +1091,7 @@ __device__ int clip_list(WarpPoly<R>& P, const ClipParams& cp, const CellCtx& cc
 }
 
 template <typename R, int MODE>
-__global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
+__global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, 4)
     clip_kernel(ClipParams cp) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpPoly<R>* polys = reinterpret_cast<WarpPoly<R>*>(smem_raw);
@@ -1114,7 +1137,10 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
             int nprev = min(cp.fcnt[i], FCAP);
             rc = clip_list(P, cp, cc, cp.fcol + i * FCAP, nprev, lane, bad);
         }
-        if (rc == CLIP_NONE || rc == CLIP_CUT)
+        // the k nearest seeds start every cell of the first diagram, and any cell with
+        // no facets in the previous one
+        const bool use_knn = !cp.facets_valid || cp.fcnt[i] == 0;
+        if (use_knn && (rc == CLIP_NONE || rc == CLIP_CUT))
             rc = clip_list(P, cp, cc, cp.knn + i * cp.k, cp.k, lane, bad);
         if (rc == CLIP_EMPTY) st |= CS_EMPTY;
         if (rc == CLIP_CAP) st |= CS_CAPACITY | CS_CAP_POLY;
@@ -1329,6 +1355,8 @@ static int launch_clip(const ClipParams& cp, cudaStream_t s) {
     if (blocks == 0) {
         SDOT_CUDA_TRY(cudaFuncSetAttribute(clip_kernel<R, MODE>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        SDOT_CUDA_TRY(cudaFuncSetAttribute(clip_kernel<R, MODE>,
+                                           cudaFuncAttributePreferredSharedMemoryCarveout, 100));
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, clip_kernel<R, MODE>,
                                                       WARPS_PER_BLOCK * 32, smem);
