@@ -52,6 +52,8 @@ def parse():
                     help="skip the single FP64 solve reported beside the mixed one")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--laguerre-once", action="store_true",
+                    help="profiling aid: build the context and evaluate one diagram at psi = 0")
     return ap.parse_args()
 
 
@@ -342,9 +344,26 @@ def run_native(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def laguerre_once(args):
+    import torch
+
+    from paper_2110_08868_gb300 import binding as B
+    from paper_2110_08868_gb300 import ics
+
+    y, nu, L = ics.make_config(**ics.CONFIGS[args.workload])
+    s = B.Solver(torch.from_numpy(y).cuda(), [L, L, L], precision=args.precision)
+    g = s.laguerre(allow_empty=True)
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": args.workload, "N": int(y.shape[0]),
+                      "sum_vol_rel_err": float(g["vol"].sum() / L ** 3 - 1.0)}))
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.laguerre_once:
+        laguerre_once(args)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:
