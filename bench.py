@@ -279,13 +279,19 @@ def run_native(args, rank, world, local):
         return
 
     st = stats[-1]
-    evals = max(st["laguerre_evals"], 1)
-    pass1_ms = st["ms_pass"][0] / evals
+    if args.precision == "mixed":
+        n1 = sum(x["evals_fp32"] for x in stats)
+        pass1_ms = sum(x["ms_pass1_fp32"] for x in stats) / max(n1, 1)
+    else:
+        n1 = sum(x["laguerre_evals"] for x in stats)
+        pass1_ms = sum(x["ms_pass"][0] for x in stats) / max(n1, 1)
     peaks = measured_peaks()
     clock_ghz = (clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)) / 1e3
     peak_tf = N_SM * FP32_LANES_PER_SM * 2 * clock_ghz / 1e3
     achieved_tf = N * FLOP_PER_CELL / (pass1_ms / 1e3) / 1e12
-    roofline = {"kernel": "clip_kernel<float,certify> (first clipping pass)", "bound": "alu",
+    roofline = {"kernel": "clip_kernel<float,certify> (first clipping pass)" if args.precision ==
+                "mixed" else "clip_kernel<double,certify> (first clipping pass)", "bound": "alu",
+                "launches_timed": n1,
                 "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                 "frac": achieved_tf / peak_tf, "traffic": None,
                 "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {clock_ghz:.3f} GHz "
@@ -311,7 +317,8 @@ def run_native(args, rank, world, local):
                                                    "ms_pass")},
              "step": {k: st[k] for k in ("newton_iters", "laguerre_evals", "cg_iters",
                                          "requeued", "reclipped_fp64", "ms_knn", "ms_clip",
-                                         "ms_cg", "ms_total", "ms_pass")},
+                                         "ms_cg", "ms_total", "ms_pass", "refined_fp64",
+                                         "max_rel_err")},
              "roofline_pcg": spmv}
     if not args.no_fp64_compare and args.precision == "mixed":
         opt64 = B.sdot_default_options(precision="fp64")

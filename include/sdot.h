@@ -95,6 +95,9 @@ typedef struct {
     double ms_total;         /* wall time of the solve */
     double ms_pass[3];       /* device time per clipping pass, summed over evaluations:
                                 security-test pass, re-queue pass, FP64 re-clip pass */
+    int refined_fp64;        /* 1 if a mixed-precision solve finished with FP64 evaluations */
+    int evals_fp32;          /* evaluations with FP32 clipping */
+    double ms_pass1_fp32;    /* device time of their first (security-test) pass */
 } sdot_stats;
 
 typedef struct sdot_ctx sdot_ctx;
@@ -138,7 +141,10 @@ int sdot_laguerre(sdot_ctx* ctx, const double* psi, double* volumes, double* cen
  * Jacobi-preconditioned CG and takes the first alpha in a0, a0/2, a0/4, ... with
  * min_j V_j >= eps0 and ||nu - V||_2 <= (1 - alpha/2) ||nu - V(psi)||_2, where
  * eps0 = 1/2 min(min_j V_j(psi0), min_j nu_j); a0 = 1, or min(1, 4 alpha_prev) after
- * the first step when opt.warm_alpha is set. The result keeps sum(psi) = 0.
+ * the first step when opt.warm_alpha is set. In mixed precision, when the error is
+ * below 1e-2 and no step of at least 1/16 is accepted (FP32 rounding is the floor),
+ * the remaining evaluations are done in FP64 (st->refined_fp64 = 1). The result keeps
+ * sum(psi) = 0.
  * st may be NULL.
  */
 int sdot_solve(sdot_ctx* ctx, double tol, const double* psi0, sdot_stats* st);

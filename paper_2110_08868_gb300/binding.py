@@ -48,7 +48,9 @@ class sdot_stats(ctypes.Structure):
                 ("last_alpha", ctypes.c_double), ("requeued", ctypes.c_int64),
                 ("reclipped_fp64", ctypes.c_int64), ("ms_knn", ctypes.c_double),
                 ("ms_clip", ctypes.c_double), ("ms_cg", ctypes.c_double),
-                ("ms_total", ctypes.c_double), ("ms_pass", ctypes.c_double * 3)]
+                ("ms_total", ctypes.c_double), ("ms_pass", ctypes.c_double * 3),
+                ("refined_fp64", ctypes.c_int), ("evals_fp32", ctypes.c_int),
+                ("ms_pass1_fp32", ctypes.c_double)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}

@@ -101,8 +101,9 @@ int check_opt(const sdot_options& o) {
     return SDOT_OK;
 }
 
-int eval_at(sdot_ctx* c, const double* psi_sorted, EvalResult* r) {
-    int rc = evaluate_cells(c->d, psi_sorted, c->opt.precision, r, c->stream);
+int eval_at(sdot_ctx* c, const double* psi_sorted, EvalResult* r, int precision = -1) {
+    int rc = evaluate_cells(c->d, psi_sorted, precision < 0 ? c->opt.precision : precision, r,
+                            c->stream);
     if (rc) return rc;
     return SDOT_OK;
 }
@@ -440,6 +441,10 @@ int sdot_solve(sdot_ctx* c, double tol, const double* psi0, sdot_stats* st) {
     S.laguerre_evals = 1;
     S.ms_clip += ev.ms;
     for (int q = 0; q < 3; q++) S.ms_pass[q] += ev.ms_pass[q];
+    if (c->opt.precision == SDOT_PREC_MIXED) {
+        S.evals_fp32++;
+        S.ms_pass1_fp32 += ev.ms_pass[0];
+    }
     if ((rc = eval_status(ev, "sdot_solve"))) return rc;
     if (ev.n_empty > 0) {
         set_error("sdot_solve: the initial psi has empty cells");
@@ -453,6 +458,7 @@ int sdot_solve(sdot_ctx* c, double tol, const double* psi0, sdot_stats* st) {
     cudaEventCreate(&c1);
     int it = 0;
     double alpha = 1.0;
+    int prec = c->opt.precision;  // precision of the current evaluations
     rc = SDOT_OK;
     log_iter(c, it, ev, 0.0, 0, 0.0, 0);
     while (ev.max_rel_err > tol) {
@@ -472,36 +478,23 @@ int sdot_solve(sdot_ctx* c, double tol, const double* psi0, sdot_stats* st) {
         cudaEventElapsedTime(&ms, c0, c1);
         S.ms_cg += ms;
         S.cg_iters += cg_it;
-        if (c->opt.verbose > 1) {
-            std::vector<double> h((size_t)d.N), dg((size_t)d.N);
-            cudaMemcpy(h.data(), d.x, (size_t)d.N * 8, cudaMemcpyDeviceToHost);
-            cudaMemcpy(dg.data(), d.dinv, (size_t)d.N * 8, cudaMemcpyDeviceToHost);
-            double mx = 0, mn = 0;
-            int64_t nonfinite = 0, zero_dinv = 0;
-            for (int64_t t = 0; t < d.N; t++) {
-                if (!isfinite(h[t])) nonfinite++;
-                else { mx = fmax(mx, h[t]); mn = fmin(mn, h[t]); }
-                if (dg[t] == 0.0) zero_dinv++;
-            }
-            fprintf(stderr,
-                    "{\"pcg_iters\": %d, \"pcg_rel_res\": %.3e, \"nnz\": %lld, \"delta_min\": %.3e, "
-                    "\"delta_max\": %.3e, \"nonfinite\": %lld, \"zero_diag\": %lld}\n",
-                    cg_it, cg_res, (long long)c->nnz, mn, mx, (long long)nonfinite,
-                    (long long)zero_dinv);
-        }
-        // damping: alpha = 1, 1/2, 1/4, ... (first acceptable); with alpha_warm the
+        // damping: alpha = 1, 1/2, 1/4, ... (first acceptable); with warm_alpha the
         // sequence starts at min(1, 4 alpha_prev) instead of 1
-        alpha = c->opt.warm_alpha ? fmin(1.0, 4.0 * alpha) : 1.0;
-        if (it == 0) alpha = 1.0;
+        alpha = (c->opt.warm_alpha && it > 0) ? fmin(1.0, 4.0 * alpha) : 1.0;
         int trials = 0;
+        bool refine = false;
         EvalResult et;
         while (true) {
             if ((rc = axpy_gauge(d, d.psi, d.x, alpha, d.psi_trial, s))) break;
-            if ((rc = eval_at(c, d.psi_trial, &et))) break;
+            if ((rc = eval_at(c, d.psi_trial, &et, prec))) break;
             trials++;
             S.laguerre_evals++;
             S.ms_clip += et.ms;
             for (int q = 0; q < 3; q++) S.ms_pass[q] += et.ms_pass[q];
+            if (prec == SDOT_PREC_MIXED) {
+                S.evals_fp32++;
+                S.ms_pass1_fp32 += et.ms_pass[0];
+            }
             bool valid = !(et.flags & (CS_TOO_LARGE | CS_CAPACITY));
             if (c->opt.verbose > 1)
                 fprintf(stderr,
@@ -512,6 +505,13 @@ int sdot_solve(sdot_ctx* c, double tol, const double* psi0, sdot_stats* st) {
                         (long long)et.reclipped);
             if (valid && et.min_vol >= eps0 && et.l2_err <= (1.0 - 0.5 * alpha) * ev.l2_err) break;
             alpha *= 0.5;
+            // FP64 refinement: in the quadratic regime (small error) a full Newton step
+            // must be accepted; if FP32 cells cannot make the residual drop, their
+            // rounding is the floor, and the remaining steps are taken in FP64
+            if (prec == SDOT_PREC_MIXED && ev.max_rel_err < 1e-2 && alpha < 1.0 / 16) {
+                refine = true;
+                break;
+            }
             if (alpha < c->opt.alpha_min) {
                 set_error("sdot_solve: line search step below alpha_min");
                 rc = SDOT_ERR_NO_DESCENT;
@@ -519,6 +519,17 @@ int sdot_solve(sdot_ctx* c, double tol, const double* psi0, sdot_stats* st) {
             }
         }
         if (rc) break;
+        if (refine) {
+            prec = SDOT_PREC_FP64;
+            S.refined_fp64 = 1;
+            if ((rc = eval_at(c, d.psi, &ev, prec))) break;
+            S.laguerre_evals++;
+            S.ms_clip += ev.ms;
+            for (int q = 0; q < 3; q++) S.ms_pass[q] += ev.ms_pass[q];
+            alpha = 1.0;
+            log_iter(c, it, ev, 0.0, cg_it, cg_res, trials);
+            continue;
+        }
         double* t = d.psi;
         d.psi = d.psi_trial;
         d.psi_trial = t;

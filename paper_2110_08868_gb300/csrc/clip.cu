@@ -286,7 +286,7 @@ enum { CLIP_NONE = 0, CLIP_CUT = 1, CLIP_EMPTY = 2, CLIP_CAP = 3 };
 // planes that merely touch an edge or a corner (lattice-like degeneracy) do not cut
 template <typename R>
 __device__ __forceinline__ R class_eps() {
-    return sizeof(R) == 4 ? R(1e-6) : R(1e-13);
+    return sizeof(R) == 4 ? R(2e-7) : R(1e-13);
 }
 template <typename R>
 __device__ __forceinline__ bool beyond(const V3<R>& v, const V4<R>& pn, R plen, R& sd) {
