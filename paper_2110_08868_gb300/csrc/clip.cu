@@ -922,6 +922,27 @@ __device__ __noinline__ void integrate(WarpPoly<R>& P, const ClipParams& cp, int
                           bool& bad, uint32_t& st) {
     double vol6 = 0, mx = 0, my = 0, mz = 0, sx = 0, sy = 0, sz = 0, sabs = 0;
     constexpr int FPL = MAXP / 32;  // faces handled per lane
+    // apex of the tetrahedron fans: the centre o of the vertices' bounding box, so the
+    // determinants involve offsets of the cell's own size even when the cell lies far
+    // from its seed (no cancellation of large terms in FP32)
+    R o[3];
+    {
+        R mn[3] = {R(1e30), R(1e30), R(1e30)}, mx[3] = {R(-1e30), R(-1e30), R(-1e30)};
+        for (int s2 = lane; s2 < P.nt; s2 += 32) {
+            V3<R> v = P.v[s2];
+            mn[0] = fmin(mn[0], v.x); mx[0] = fmax(mx[0], v.x);
+            mn[1] = fmin(mn[1], v.y); mx[1] = fmax(mx[1], v.y);
+            mn[2] = fmin(mn[2], v.z); mx[2] = fmax(mx[2], v.z);
+        }
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            for (int q = 16; q > 0; q >>= 1) {
+                mn[a] = fmin(mn[a], __shfl_xor_sync(FULLMASK, mn[a], q));
+                mx[a] = fmax(mx[a], __shfl_xor_sync(FULLMASK, mx[a], q));
+            }
+            o[a] = R(0.5) * (mn[a] + mx[a]);
+        }
+    }
     int nf = 0;
     int32_t fj[FPL];
     double fc[FPL];
@@ -955,6 +976,9 @@ __device__ __noinline__ void integrate(WarpPoly<R>& P, const ClipParams& cp, int
         // walk the cycle: the entry after (x, y) is the one whose x equals y
         int cur = 0;
         V3<R> v0 = P.v[ent[0] >> 16];
+        v0.x -= o[0];
+        v0.y -= o[1];
+        v0.z -= o[2];
         V3<R> vp = v0;
         R Sx = 0, Sy = 0, Sz = 0;
         bool ok = true;
@@ -966,6 +990,9 @@ __device__ __noinline__ void integrate(WarpPoly<R>& P, const ClipParams& cp, int
             if (nxt < 0 || nxt == 0) { ok = false; break; }
             cur = nxt;
             V3<R> vc = P.v[ent[cur] >> 16];
+            vc.x -= o[0];
+            vc.y -= o[1];
+            vc.z -= o[2];
             if (step >= 2) {
                 // fan triangle (v0, vp, vc) and tetrahedron (0, v0, vp, vc)
                 R ax = vp.x - v0.x, ay = vp.y - v0.y, az = vp.z - v0.z;
@@ -974,7 +1001,7 @@ __device__ __noinline__ void integrate(WarpPoly<R>& P, const ClipParams& cp, int
                 Sx += cx;
                 Sy += cy;
                 Sz += cz;
-                // det(v0, vp, vc) = v0 . (vp x vc) = v0 . ((vp - v0) x (vc - v0))
+                // 6 |tet(o, v0, vp, vc)| = det(v0, vp, vc) with vertices relative to o
                 double d6 = (double)(v0.x * cx + v0.y * cy + v0.z * cz);
                 vol6 += d6;
                 mx += d6 * ((double)v0.x + (double)vp.x + (double)vc.x);
@@ -1031,6 +1058,10 @@ __device__ __noinline__ void integrate(WarpPoly<R>& P, const ClipParams& cp, int
     if (!(closure <= tol * sabs)) bad = true;
     double vol = vol6 / 6.0;
     if (!(vol > 0.0) || !isfinite(vol)) bad = true;
+    // first moment about the seed = moment about o + o V (mx.. hold 24 x moment about o)
+    mx += 24.0 * (double)o[0] * vol;
+    my += 24.0 * (double)o[1] * vol;
+    mz += 24.0 * (double)o[2] * vol;
     bad = __any_sync(FULLMASK, bad);
     uint32_t stall = __reduce_or_sync(FULLMASK, st);
     st = stall;
