@@ -175,6 +175,30 @@ int sdot_knn(sdot_ctx* ctx, int32_t* nbr);
  * periodic image, 32/64/128 capacity detail (polytope / face / traversal stack). */
 int sdot_cell_status(sdot_ctx* ctx, uint8_t* status);
 
+/*
+ * sdot_knn_static — the kNN lists of sdot_create/sdot_knn computed without allocating
+ * any device memory (the paper has no counterpart; this serves callers that cannot
+ * allocate on their path, e.g. code running inside another framework's memory pool or
+ * under a fixed device-memory budget, or latency-critical code that must not call
+ * cudaMalloc/cudaFree because they can synchronise the device).
+ *  pos:    N x 3 doubles in device (or managed) memory, each coordinate in [0, box[a]).
+ *  N, k:   2 <= N <= SDOT_STATIC_MAX_N, 1 <= k <= SDOT_STATIC_MAX_K, k < N; larger
+ *          requests return SDOT_ERR_ARG with a message.
+ *  box:    3 box lengths (host memory).
+ *  nbr:    N x k int32 out, device (or managed) memory; same contents as sdot_knn.
+ *  stream: cudaStream_t for the work (NULL: legacy default stream); the call returns
+ *          after synchronising it.
+ * All scratch lives in one fixed array of about 6 MB declared in the library, which
+ * every GPU that loads the library keeps until the process exits. The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress), so make that
+ * first call before any stream capture. Calls share the array and it keeps the last
+ * call's contents: calls whose GPU work overlaps race, so serialise them.
+ */
+#define SDOT_STATIC_MAX_N 32768
+#define SDOT_STATIC_MAX_K 32
+int sdot_knn_static(const double* pos, int64_t N, const double box[3], int k, int32_t* nbr,
+                    void* stream);
+
 /* Number of seeds and kNN size of the context. */
 int sdot_size(const sdot_ctx* ctx, int64_t* N, int* k);
 

@@ -61,8 +61,8 @@ class sdot_stats(ctypes.Structure):
 # every symbol include/sdot.h declares
 EXPORTS = ["sdot_default_options", "sdot_create", "sdot_set_stream", "sdot_laguerre",
            "sdot_solve", "sdot_csr_copy", "sdot_get_psi", "sdot_displacement", "sdot_knn",
-           "sdot_cell_status", "sdot_size", "sdot_destroy", "sdot_kernel_launches",
-           "sdot_last_error"]
+           "sdot_cell_status", "sdot_knn_static", "sdot_size", "sdot_destroy",
+           "sdot_kernel_launches", "sdot_last_error"]
 
 _lib = None
 
@@ -92,6 +92,7 @@ def load(path=LIB_PATH):
     lib.sdot_displacement.argtypes = [P, P]
     lib.sdot_knn.argtypes = [P, P]
     lib.sdot_cell_status.argtypes = [P, P]
+    lib.sdot_knn_static.argtypes = [P, I64, P, I, P, P]
     lib.sdot_size.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I)]
     lib.sdot_destroy.argtypes = [P]
     lib.sdot_destroy.restype = None
@@ -189,6 +190,18 @@ def sdot_knn(ctx, nbr):
 
 def sdot_cell_status(ctx, status):
     return load().sdot_cell_status(ctx, _ptr(status, np.uint8))
+
+
+SDOT_STATIC_MAX_N = 32768
+SDOT_STATIC_MAX_K = 32
+
+
+def sdot_knn_static(pos, box, k, nbr, stream=None):
+    """kNN lists without device allocation (pos, nbr: CUDA tensors; see include/sdot.h)."""
+    b = np.ascontiguousarray(np.broadcast_to(np.asarray(box, dtype=np.float64), (3,)))
+    h = getattr(stream, "cuda_stream", stream)
+    return load().sdot_knn_static(_ptr(pos), int(pos.shape[0]), ctypes.c_void_p(b.ctypes.data),
+                                  int(k), _ptr(nbr, np.int32), ctypes.c_void_p(h) if h else None)
 
 
 def sdot_size(ctx):
