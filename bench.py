@@ -127,6 +127,26 @@ def measured_peaks():
         return {}
 
 
+def max_over_ranks(ms, dist):
+    """Step time of the slowest rank (the whole job's time); ms when running alone."""
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_config(workload, rank, world):
+    """Replicas only: every rank solves its own box (seed offset by 1000 x rank)."""
+    from paper_2110_08868_gb300 import ics
+
+    cfg = dict(ics.CONFIGS[workload])
+    if world > 1:
+        cfg["seed"] = cfg["seed"] + 1000 * rank
+    return cfg
+
+
 def cpu_baseline(workload, seconds=12.0):
     """The CPU oracle as it stands, on a bounded sample of the workload's cells."""
     sys.path.insert(0, os.path.join(ROOT, "oracle"))
@@ -185,10 +205,7 @@ def run_native(args, rank, world, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("gloo")
-    cfg = dict(ics.CONFIGS[args.workload])
-    if world > 1:
-        cfg["seed"] = cfg["seed"] + 1000 * rank  # replicas: one independent box per rank
-    y, nu, L = ics.make_config(**cfg)
+    y, nu, L = ics.make_config(**replica_config(args.workload, rank, world))
     N = int(y.shape[0])
     box = [L, L, L]
     pos_dev = torch.from_numpy(y).cuda()
@@ -248,10 +265,7 @@ def run_native(args, rank, world, local):
     launches = B.sdot_kernel_launches() - l0
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1) / args.steps
-    t = torch.tensor([ms], dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, dist)
     value = world * N / (ms_max / 1e3)
 
     # e2e through host buffers (pinned), copies inside the timed region
@@ -266,11 +280,8 @@ def run_native(args, rank, world, local):
         for _ in range(args.steps):
             one_step(pos_host, disp_host, psi_host)
         torch.cuda.synchronize()
-        e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
-        te = torch.tensor([e_ms], dtype=torch.float64)
-        if dist is not None:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * N / (float(te.item()) / 1e3), "unit": "cells/s",
+        e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps, dist)
+        e2e = {"value": world * N / (e_ms / 1e3), "unit": "cells/s",
                "h2d_bytes_per_step": N * 3 * 8 + N * 8, "d2h_bytes_per_step": N * 3 * 8}
 
     if rank != 0:

@@ -677,7 +677,10 @@ __device__ __forceinline__ bool node_pruned(const ClipParams& cp, const Bounds& 
     return val2 > margin2;
 }
 
-// conservative FP32 test: can the plane (n, w) reach the polytope's bounding box?
+// conservative FP32 test: can the plane (n, w) reach the polytope? Two valid upper
+// bounds of max_vertex v.n are used, the support of the bounding box and that of the
+// ball of radius Rc around the box centre c; the plane is a candidate only if both
+// reach it.
 __device__ __forceinline__ bool box_may_cut(const Bounds& b, float nx, float ny, float nz,
                                             float w) {
     float sx = nx > 0.f ? nx * b.bmax[0] : nx * b.bmin[0];
@@ -685,7 +688,11 @@ __device__ __forceinline__ bool box_may_cut(const Bounds& b, float nx, float ny,
     float sz = nz > 0.f ? nz * b.bmax[2] : nz * b.bmin[2];
     float S = sx + sy + sz;
     float margin = 2e-5f * (fabsf(sx) + fabsf(sy) + fabsf(sz) + fabsf(w)) + 1e-5f;
-    return S > w - margin;
+    if (!(S > w - margin)) return false;
+    float cn = b.c[0] * nx + b.c[1] * ny + b.c[2] * nz;
+    float rn = b.Rc * sqrtf(nx * nx + ny * ny + nz * nz);
+    float margin2 = 2e-5f * (fabsf(cn) + rn + fabsf(w)) + 1e-5f;
+    return cn + rn > w - margin2;
 }
 
 enum { MODE_CERTIFY = 0, MODE_FULL = 1 };

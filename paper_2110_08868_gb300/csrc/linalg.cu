@@ -98,7 +98,7 @@ int csr_count(DeviceState& d, int64_t* nnz_out, cudaStream_t s) {
     SDOT_CUDA_TRY(cudaGetLastError());
     // row_ptr = exclusive scan over N+1 entries (rowcnt[N] == 0)
     SDOT_CUDA_TRY(cudaMemsetAsync(d.rowcnt + N, 0, 4, s));
-    int rc = scan_exclusive_i32_to_i64(d.rowcnt, d.row_ptr, N + 1, d.partials + 4096, s);
+    int rc = scan_exclusive_i32_to_i64(d.rowcnt, d.row_ptr, N + 1, d.partials + 65536, s);
     if (rc) return rc;
     int64_t nnz = 0;
     SDOT_CUDA_TRY(cudaMemcpyAsync(&nnz, d.row_ptr + N, 8, cudaMemcpyDeviceToHost, s));
@@ -158,7 +158,7 @@ int assemble_csr_user(DeviceState& d, int64_t nnz, cudaStream_t s) {
     note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
     SDOT_CUDA_TRY(cudaMemsetAsync(d.rowcnt + N, 0, 4, s));
-    int rc = scan_exclusive_i32_to_i64(d.rowcnt, d.row_ptr_u, N + 1, d.partials + 4096, s);
+    int rc = scan_exclusive_i32_to_i64(d.rowcnt, d.row_ptr_u, N + 1, d.partials + 65536, s);
     if (rc) return rc;
     csr_user_fill<<<nb, 256, 0, s>>>(d.row_ptr, d.col, d.val, d.perm, N, d.row_ptr_u, d.col_u,
                                      d.val_u);
@@ -305,7 +305,9 @@ __global__ void partial_final_kernel(const double* __restrict__ part, int nb, in
 int pcg_solve(DeviceState& d, double rtol, int maxit, int* iters, double* rel_res,
               cudaStream_t s) {
     const int64_t N = d.N;
-    const int nb = 2 * num_sms();
+    // memory-bound loops: enough resident warps (8 blocks of 8 warps per SM) to cover
+    // the dependent row_ptr -> col -> p[col] loads of the SpMV
+    const int nb = 8 * num_sms();
     double* partA = d.partials;
     double* partB[2] = {d.partials + nb, d.partials + 3 * nb};
     double* hs = d.scal + 8;
