@@ -260,7 +260,7 @@ int sdot_create(const double* pos, const double* mass, int64_t N, const double b
         G[a] = (int)g;
         ncell *= G[a];
     }
-    if ((rc = alloc_n(c, &d.pos, N)) || (rc = alloc_n(c, &d.posf, N)) || (rc = alloc_n(c, &d.pslo, N)) ||
+    if ((rc = alloc_n(c, &d.pos, N)) || (rc = alloc_n(c, &d.posf, N)) || (rc = alloc_n(c, &d.pslo, N)) || (rc = alloc_n(c, &d.ioff, N)) ||
         (rc = alloc_n(c, &d.leafc, N)) ||
         (rc = alloc_n(c, &d.perm, N)) || (rc = alloc_n(c, &d.iperm, N)) ||
         (rc = alloc_n(c, &d.nu, N)) || (rc = alloc_n(c, &d.psi, N)) ||

@@ -108,6 +108,8 @@ struct ClipParams {
     int64_t nwork;
     unsigned long long* counters64;  // diagnostic work counters (8)
     const float* pslo;               // low part of psi/a^2
+    const uint4* ioff;               // grid-cell offsets, 32-bit fixed point
+    float hfix[3];                   // cell size / a / 2^32 (fixed-point unit)
     const int32_t* leafc;            // grid cell of each seed, x | y << 10 | z << 20
     int facets_valid;                // fcnt/fcol hold the previous diagram's facets
 };
@@ -493,6 +495,7 @@ __device__ __forceinline__ void make_plane(const ClipParams& cp, const Pos4& yi,
 struct SeedRef {
     int c[3];
     float off[3];
+    uint32_t io[3];
     float phi, plo;
 };
 
@@ -508,7 +511,37 @@ __device__ __forceinline__ SeedRef load_seed(const ClipParams& cp, int64_t i) {
     r.off[2] = p.z;
     r.phi = p.w;
     r.plo = cp.pslo[i];
+    uint4 q = cp.ioff[i];
+    r.io[0] = q.x;
+    r.io[1] = q.y;
+    r.io[2] = q.z;
     return r;
+}
+
+// FP32 plane of seed j for cell i with the seed difference taken exactly: grid-cell
+// difference and 32-bit fixed-point offsets combine into one int64 per axis, rounded
+// once to FP32. Close seeds (clumps) keep full FP32 relative precision in d, which
+// float offsets would lose (their absolute error would be a large part of d).
+__device__ __forceinline__ void plane_fix(const ClipParams& cp, const SeedRef& si, int32_t j,
+                                          float& nx, float& ny, float& nz, float& w) {
+    int lc = cp.leafc[j];
+    uint4 q = cp.ioff[j];
+    int cj[3] = {lc & 1023, (lc >> 10) & 1023, (lc >> 20) & 1023};
+    uint32_t oj[3] = {q.x, q.y, q.z};
+    float d[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        int dc = cj[a] - si.c[a];
+        if (2 * dc > cp.G[a]) dc -= cp.G[a];
+        else if (2 * dc < -cp.G[a]) dc += cp.G[a];
+        long long di = ((long long)dc << 32) + (long long)oj[a] - (long long)si.io[a];
+        d[a] = wrapf((float)di * cp.hfix[a], cp.Lt[a], cp.halfLt[a]);
+    }
+    nx = d[0];
+    ny = d[1];
+    nz = d[2];
+    float4 pj = cp.posf[j];
+    w = 0.5f * (nx * nx + ny * ny + nz * nz) + ((si.phi - pj.w) + (si.plo - cp.pslo[j]));
 }
 
 // FP32 plane of seed j for cell i from grid-local coordinates: the integer part of
@@ -717,7 +750,7 @@ __device__ __forceinline__ void build_plane(const ClipParams& cp, const CellCtx&
         pn.w = (R)wd;
     } else {
         float nx, ny, nz, w;
-        plane_f32(cp, cc.si, j, nx, ny, nz, w);
+        plane_fix(cp, cc.si, j, nx, ny, nz, w);
         pn.x = (R)nx;
         pn.y = (R)ny;
         pn.z = (R)nz;
@@ -1245,7 +1278,8 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, 4)
 __global__ void posf_kernel(const Pos4* __restrict__ pos, const double* __restrict__ psi,
                             int64_t N, double inv_a, double inv_a2, double hx, double hy,
                             double hz, int Gx, int Gy, int Gz, float4* __restrict__ posf,
-                            float* __restrict__ pslo, int32_t* __restrict__ leafc) {
+                            float* __restrict__ pslo, int32_t* __restrict__ leafc,
+                            uint4* __restrict__ ioff) {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= N) return;
     Pos4 y = pos[s];
@@ -1254,17 +1288,23 @@ __global__ void posf_kernel(const Pos4* __restrict__ pos, const double* __restri
     double p[3] = {y.x, y.y, y.z};
     int c[3];
     float off[3];
+    uint32_t io[3];
     for (int a = 0; a < 3; a++) {
         int cc = (int)floor(p[a] / h[a]);
         cc = cc < 0 ? 0 : (cc >= G[a] ? G[a] - 1 : cc);
         c[a] = cc;
-        off[a] = (float)((p[a] - cc * h[a]) * inv_a);
+        double f = p[a] - cc * h[a];
+        off[a] = (float)(f * inv_a);
+        double fx = floor(f / h[a] * 4294967296.0);
+        fx = fx < 0.0 ? 0.0 : (fx > 4294967295.0 ? 4294967295.0 : fx);
+        io[a] = (uint32_t)fx;
     }
     double q = psi[s] * inv_a2;
     float hi = (float)q;
     posf[s] = make_float4(off[0], off[1], off[2], hi);
     pslo[s] = (float)(q - (double)hi);
     leafc[s] = c[0] | (c[1] << 10) | (c[2] << 20);
+    ioff[s] = make_uint4(io[0], io[1], io[2], 0u);
 }
 
 __global__ void leaf_max_kernel(const int32_t* __restrict__ cell_start, int64_t ncell,
@@ -1295,7 +1335,7 @@ int build_pyramid(DeviceState& d, const double* psi, cudaStream_t s) {
     const int64_t N = d.N;
     posf_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(
         d.pos, psi, N, 1.0 / d.a, 1.0 / (d.a * d.a), d.grid.h[0], d.grid.h[1], d.grid.h[2],
-        d.grid.G[0], d.grid.G[1], d.grid.G[2], d.posf, d.pslo, d.leafc);
+        d.grid.G[0], d.grid.G[1], d.grid.G[2], d.posf, d.pslo, d.leafc, d.ioff);
         note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
     Pyramid& P = d.pyr;
@@ -1431,6 +1471,8 @@ int evaluate_cells(DeviceState& d, const double* psi, int precision, EvalResult*
     cp.pos = d.pos;
     cp.posf = d.posf;
     cp.pslo = d.pslo;
+    cp.ioff = d.ioff;
+    for (int a = 0; a < 3; a++) cp.hfix[a] = (float)(d.grid.h[a] / d.a / 4294967296.0);
     cp.leafc = d.leafc;
     cp.facets_valid = d.facets_valid;
     cp.psi = psi;

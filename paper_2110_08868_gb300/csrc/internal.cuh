@@ -75,6 +75,7 @@ struct DeviceState {
     Pos4* pos;             // sorted positions; w = caller index (exact in fp64)
     float4* posf;             // (offset in grid cell / a, psi/a^2 hi), per evaluation
     float* pslo;              // psi/a^2 lo part (psi/a^2 = hi + lo)
+    uint4* ioff;              // offset in the grid cell as 32-bit fixed point (x, y, z, 0)
     int32_t* leafc;           // grid cell of each seed: x | y << 10 | z << 20
     int facets_valid;         // fcnt/fcol hold a complete previous diagram
     int32_t* perm;            // sorted -> caller index
