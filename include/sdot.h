@@ -143,8 +143,8 @@ int sdot_laguerre(sdot_ctx* ctx, const double* psi, double* volumes, double* cen
  * eps0 = 1/2 min(min_j V_j(psi0), min_j nu_j); a0 = 1, or min(1, 4 alpha_prev) after
  * the first step when opt.warm_alpha is set. In mixed precision, when the error is
  * below 1e-3 and the full step alpha = 1 is rejected (FP32 rounding is the floor),
- * the same step is retried with FP64 cells and the remaining evaluations stay FP64
- * (st->refined_fp64 = 1). The result keeps sum(psi) = 0.
+ * the current point is evaluated again with FP64 cells and the remaining Newton steps
+ * stay FP64 (st->refined_fp64 = 1). The result keeps sum(psi) = 0.
  * st may be NULL.
  */
 int sdot_solve(sdot_ctx* ctx, double tol, const double* psi0, sdot_stats* st);

@@ -482,6 +482,7 @@ int sdot_solve(sdot_ctx* c, double tol, const double* psi0, sdot_stats* st) {
         // sequence starts at min(1, 4 alpha_prev) instead of 1
         alpha = (c->opt.warm_alpha && it > 0) ? fmin(1.0, 4.0 * alpha) : 1.0;
         int trials = 0;
+        bool refine = false;
         EvalResult et;
         while (true) {
             if ((rc = axpy_gauge(d, d.psi, d.x, alpha, d.psi_trial, s))) break;
@@ -506,13 +507,11 @@ int sdot_solve(sdot_ctx* c, double tol, const double* psi0, sdot_stats* st) {
             alpha *= 0.5;
             // FP64 refinement: in the quadratic regime (small error) the full Newton
             // step must be accepted; if the FP32 cells cannot make the residual drop,
-            // their rounding is the floor: the same direction is retried at alpha = 1
-            // with FP64 cells, and the remaining steps stay in FP64
+            // their rounding is the floor: the current point is evaluated again with
+            // FP64 cells and the remaining Newton steps stay in FP64
             if (prec == SDOT_PREC_MIXED && ev.max_rel_err < 1e-3 && alpha < 1.0) {
-                prec = SDOT_PREC_FP64;
-                S.refined_fp64 = 1;
-                alpha = 1.0;
-                continue;
+                refine = true;
+                break;
             }
             if (alpha < c->opt.alpha_min) {
                 set_error("sdot_solve: line search step below alpha_min");
@@ -521,6 +520,17 @@ int sdot_solve(sdot_ctx* c, double tol, const double* psi0, sdot_stats* st) {
             }
         }
         if (rc) break;
+        if (refine) {
+            prec = SDOT_PREC_FP64;
+            S.refined_fp64 = 1;
+            if ((rc = eval_at(c, d.psi, &ev, prec))) break;
+            S.laguerre_evals++;
+            S.ms_clip += ev.ms;
+            for (int q = 0; q < 3; q++) S.ms_pass[q] += ev.ms_pass[q];
+            alpha = 1.0;
+            log_iter(c, it, ev, 0.0, cg_it, cg_res, trials);
+            continue;
+        }
         double* t = d.psi;
         d.psi = d.psi_trial;
         d.psi_trial = t;
