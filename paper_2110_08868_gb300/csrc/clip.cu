@@ -12,7 +12,8 @@
 // vertices (one ballot), the removed vertices' dual edges whose reverse edge is
 // not removed form the boundary cycle, and every boundary edge (a -> b) yields the
 // new vertex (a, b, new plane). Integration walks each face's vertex cycle and
-// sums fan tetrahedra from the seed (volume, first moment, area vector).
+// sums fan tetrahedra from the centre of the vertices' bounding box (volume,
+// first moment, area vector).
 //
 // Neighbour search: the k nearest seeds first, then a security test. The test
 // walks a pyramid of per-node upper bounds of psi and proves, node by node, that no
@@ -24,9 +25,15 @@
 //     1/2 u^2 - 1/2 |z|^2 - R_z dmax - (psimax_B - psi_i) >= 0.
 // A cell whose test finds a seed that actually cuts it is re-queued; the re-queue
 // pass clips every such seed during the same walk. In mixed precision the geometry
-// runs in FP32 (planes built in FP64, sums accumulated in FP64) and cells failing
-// the consistency check (non-closed surface, broken face cycle, badly conditioned
-// vertex, capacity) are re-clipped in FP64.
+// runs in FP32 and cells failing the consistency check (non-closed surface, broken
+// face cycle, badly conditioned vertex, capacity) are re-clipped in FP64. The FP32
+// polytope is held relative to a frame origin z near the cell (its previous
+// centroid), where the bisector of seed j reads
+//     q.d_ij <= b_ij - d_ij.z,   p = z + q,
+// with the offset summed in FP64 from the exact seed difference: a cell far from its
+// own seed (pushed away by a clump) keeps vertex coordinates and plane offsets of
+// its own size, so FP32 rounding is relative to the cell, not to its distance from
+// the seed. Sums are accumulated in FP64.
 #include <float.h>
 #include <math.h>
 
@@ -155,8 +162,10 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // the box [-L/2, L/2]^3: bisectors with the seed's own six face images
+// The periodic box around the seed: the bisectors of the cell's own images at
+// +-Lt e_a, written relative to the frame origin z (zero: the seed itself).
 template <typename R>
-__device__ void poly_init(WarpPoly<R>& P, const ClipParams& cp, int lane) {
+__device__ void poly_init(WarpPoly<R>& P, const ClipParams& cp, const float* z, int lane) {
     if (lane < 6) {
         int ax = lane >> 1;
         R s = (lane & 1) ? R(-1) : R(1);
@@ -165,7 +174,7 @@ __device__ void poly_init(WarpPoly<R>& P, const ClipParams& cp, int lane) {
         pl.x = ax == 0 ? s * Lt : R(0);
         pl.y = ax == 1 ? s * Lt : R(0);
         pl.z = ax == 2 ? s * Lt : R(0);
-        pl.w = R(0.5) * Lt * Lt;
+        pl.w = R(0.5) * Lt * Lt - s * Lt * (R)z[ax];
         P.pl[lane] = pl;
         P.plen[lane] = Lt;
         P.pj[lane] = -1;
@@ -175,9 +184,9 @@ __device__ void poly_init(WarpPoly<R>& P, const ClipParams& cp, int lane) {
         uint32_t X = sx > 0 ? 0 : 1, Y = sy > 0 ? 2 : 3, Z = sz > 0 ? 4 : 5;
         P.tri[lane] = (sx * sy * sz > 0) ? pack3(X, Y, Z) : pack3(X, Z, Y);
         V3<R> v;
-        v.x = R(0.5) * (R)cp.Lt[0] * (R)sx;
-        v.y = R(0.5) * (R)cp.Lt[1] * (R)sy;
-        v.z = R(0.5) * (R)cp.Lt[2] * (R)sz;
+        v.x = R(0.5) * (R)cp.Lt[0] * (R)sx - (R)z[0];
+        v.y = R(0.5) * (R)cp.Lt[1] * (R)sy - (R)z[1];
+        v.z = R(0.5) * (R)cp.Lt[2] * (R)sz - (R)z[2];
         P.v[lane] = v;
     }
     if (lane == 0) {
@@ -518,30 +527,76 @@ __device__ __forceinline__ SeedRef load_seed(const ClipParams& cp, int64_t i) {
     return r;
 }
 
-// FP32 plane of seed j for cell i with the seed difference taken exactly: grid-cell
-// difference and 32-bit fixed-point offsets combine into one int64 per axis, rounded
-// once to FP32. Close seeds (clumps) keep full FP32 relative precision in d, which
-// float offsets would lose (their absolute error would be a large part of d).
-__device__ __forceinline__ void plane_fix(const ClipParams& cp, const SeedRef& si, int32_t j,
-                                          float& nx, float& ny, float& nz, float& w) {
+// Frame of the FP32 polytope of one cell: origin z (units of a, relative to the
+// seed), snapped to multiples of 2^-12 grid cells so that z is exact in FP64 and
+// nearly so in FP32.
+struct Frame {
+    float z[3];   // z in FP32
+    double zd[3]; // z in FP64
+};
+
+__device__ __forceinline__ Frame make_frame(const ClipParams& cp, const float* zwant) {
+    Frame f;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        float za = zwant[a];
+        if (!isfinite(za)) za = 0.f;
+        za = fminf(fmaxf(za, -cp.halfLt[a]), cp.halfLt[a]);
+        const double q = (double)cp.ht[a] * (1.0 / 4096.0);
+        f.zd[a] = (double)llrint((double)za / q) * q;
+        f.z[a] = (float)f.zd[a];
+    }
+    return f;
+}
+
+// the frame at the seed itself (FP64 cells, first diagram)
+__device__ __forceinline__ Frame seed_frame() {
+    Frame f;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        f.z[a] = 0.f;
+        f.zd[a] = 0.0;
+    }
+    return f;
+}
+
+// FP32 plane of seed j for cell i in the cell's frame, q.d <= 1/2 |d|^2 - d.z + psi_i -
+// psi_j with p = z + q. The seed difference is taken exactly: grid-cell difference
+// and 32-bit fixed-point offsets combine into one int64 per axis (minimum image on
+// the fixed-point period G 2^32). The normal d is rounded once to FP32, which moves
+// the plane by at most one rounding of |d| |q| at a vertex q of the cell; the offset
+// is summed in FP64 from the exact d and the hi + lo psi, then rounded once, so it
+// carries one rounding of its own (small) size: neither the distance of the cell
+// from its seed nor the size of d - z enters the error.
+__device__ __forceinline__ void plane_fix(const ClipParams& cp, const SeedRef& si,
+                                          const Frame& fr, int32_t j, float& nx, float& ny,
+                                          float& nz, float& w) {
     int lc = cp.leafc[j];
     uint4 q = cp.ioff[j];
     int cj[3] = {lc & 1023, (lc >> 10) & 1023, (lc >> 20) & 1023};
     uint32_t oj[3] = {q.x, q.y, q.z};
     float d[3];
+    double t = 0.0;
 #pragma unroll
     for (int a = 0; a < 3; a++) {
         int dc = cj[a] - si.c[a];
         if (2 * dc > cp.G[a]) dc -= cp.G[a];
         else if (2 * dc < -cp.G[a]) dc += cp.G[a];
         long long di = ((long long)dc << 32) + (long long)oj[a] - (long long)si.io[a];
-        d[a] = wrapf((float)di * cp.hfix[a], cp.Lt[a], cp.halfLt[a]);
+        const long long per = (long long)cp.G[a] << 32;
+        if (2 * di > per) di -= per;
+        else if (2 * di < -per) di += per;
+        d[a] = (float)di * cp.hfix[a];
+        const double dd = (double)di * (double)cp.hfix[a];
+        t = fma(dd, fma(0.5, dd, -fr.zd[a]), t);
     }
     nx = d[0];
     ny = d[1];
     nz = d[2];
     float4 pj = cp.posf[j];
-    w = 0.5f * (nx * nx + ny * ny + nz * nz) + ((si.phi - pj.w) + (si.plo - cp.pslo[j]));
+    const double dphi =
+        ((double)si.phi - (double)pj.w) + ((double)si.plo - (double)cp.pslo[j]);
+    w = (float)(t + dphi);
 }
 
 // FP32 plane of seed j for cell i from grid-local coordinates: the integer part of
@@ -591,6 +646,7 @@ __device__ __forceinline__ float circ_far(float p, float lo, float hi, float Lt)
 // Current bounds of the polytope: box [bmin, bmax], its centre c and the radius Rc of
 // the smallest ball around c holding every vertex (local coordinates, units of a).
 struct Bounds {
+    float zf[3];  // frame origin of the polytope's vertices (relative to the seed)
     float bmin[3], bmax[3];
     float c[3];
     float Rc;
@@ -605,7 +661,7 @@ __device__ void poly_bounds(const WarpPoly<R>& P, const ClipParams& cp, Bounds& 
     float mn[3] = {1e30f, 1e30f, 1e30f}, mx[3] = {-1e30f, -1e30f, -1e30f};
     for (int s = lane; s < P.nt; s += 32) {
         V3<R> v = P.v[s];
-        float vv[3] = {(float)v.x, (float)v.y, (float)v.z};
+        float vv[3] = {(float)v.x + b.zf[0], (float)v.y + b.zf[1], (float)v.z + b.zf[2]};
 #pragma unroll
         for (int a = 0; a < 3; a++) {
             mn[a] = fminf(mn[a], vv[a]);
@@ -625,7 +681,8 @@ __device__ void poly_bounds(const WarpPoly<R>& P, const ClipParams& cp, Bounds& 
     float r2 = 0.f;
     for (int s = lane; s < P.nt; s += 32) {
         V3<R> v = P.v[s];
-        float dx = (float)v.x - b.c[0], dy = (float)v.y - b.c[1], dz = (float)v.z - b.c[2];
+        float dx = ((float)v.x + b.zf[0]) - b.c[0], dy = ((float)v.y + b.zf[1]) - b.c[1],
+              dz = ((float)v.z + b.zf[2]) - b.c[2];
         r2 = fmaxf(r2, dx * dx + dy * dy + dz * dz);
     }
     r2 = warp_max(r2);
@@ -736,6 +793,7 @@ struct CellCtx {
     Pos4 yi;      // FP64 seed (FP64 planes)
     double psii;  // FP64 psi_i
     SeedRef si;   // grid-local seed (FP32 planes)
+    Frame fr;     // frame of the polytope (the seed itself for FP64 cells)
 };
 
 template <typename R>
@@ -750,7 +808,7 @@ __device__ __forceinline__ void build_plane(const ClipParams& cp, const CellCtx&
         pn.w = (R)wd;
     } else {
         float nx, ny, nz, w;
-        plane_fix(cp, cc.si, j, nx, ny, nz, w);
+        plane_fix(cp, cc.si, cc.fr, j, nx, ny, nz, w);
         pn.x = (R)nx;
         pn.y = (R)ny;
         pn.z = (R)nz;
@@ -956,10 +1014,13 @@ __device__ bool traverse(WarpPoly<R>& P, const ClipParams& cp, const CellCtx& cc
     return true;
 }
 
-// Integrate the polytope and write the outputs of cell i.
+// Integrate the polytope and write the outputs of cell i; cen receives the centroid
+// relative to the seed (units of a, every lane) and the return value says whether it
+// is valid (positive finite volume).
 template <typename R>
-__device__ __noinline__ void integrate(WarpPoly<R>& P, const ClipParams& cp, int64_t i, int lane,
-                          bool& bad, uint32_t& st) {
+__device__ __noinline__ bool integrate(WarpPoly<R>& P, const ClipParams& cp, const Frame& fr,
+                                       int64_t i, int lane, bool& bad, uint32_t& st,
+                                       float* cen) {
     double vol6 = 0, mx = 0, my = 0, mz = 0, sx = 0, sy = 0, sz = 0, sabs = 0;
     constexpr int FPL = MAXP / 32;  // faces handled per lane
     // apex of the tetrahedron fans: the centre o of the vertices' bounding box, so the
@@ -1098,29 +1159,53 @@ __device__ __noinline__ void integrate(WarpPoly<R>& P, const ClipParams& cp, int
     if (!(closure <= tol * sabs)) bad = true;
     double vol = vol6 / 6.0;
     if (!(vol > 0.0) || !isfinite(vol)) bad = true;
-    // first moment about the seed = moment about o + o V (mx.. hold 24 x moment about o)
-    mx += 24.0 * (double)o[0] * vol;
-    my += 24.0 * (double)o[1] * vol;
-    mz += 24.0 * (double)o[2] * vol;
+    // first moment about the seed = moment about o + (z + o) V (mx.. hold 24 x moment
+    // about o; o is relative to the frame origin z)
+    mx += 24.0 * (fr.zd[0] + (double)o[0]) * vol;
+    my += 24.0 * (fr.zd[1] + (double)o[1]) * vol;
+    mz += 24.0 * (fr.zd[2] + (double)o[2]) * vol;
     bad = __any_sync(FULLMASK, bad);
     uint32_t stall = __reduce_or_sync(FULLMASK, st);
     st = stall;
+    const double mm[3] = {mx / 24.0, my / 24.0, mz / 24.0};
+    const bool valid = vol > 0.0 && isfinite(vol);
+    if (valid)
+        for (int a = 0; a < 3; a++) cen[a] = (float)(mm[a] / vol);
     if (lane == 0) {
         double a3 = cp.a * cp.a * cp.a;
         double a4 = a3 * cp.a;
-        double mm[3] = {mx / 24.0, my / 24.0, mz / 24.0};
         cp.vol[i] = vol * a3;
         cp.m1[3 * i + 0] = mm[0] * a4;
         cp.m1[3 * i + 1] = mm[1] * a4;
         cp.m1[3 * i + 2] = mm[2] * a4;
         cp.fcnt[i] = total > FCAP ? FCAP : total;
-        if (vol > 0.0 && isfinite(vol)) {
-            cp.anchor[3 * i + 0] = (float)(mm[0] / vol);
-            cp.anchor[3 * i + 1] = (float)(mm[1] / vol);
-            cp.anchor[3 * i + 2] = (float)(mm[2] / vol);
+        if (valid) {
+            cp.anchor[3 * i + 0] = cen[0];
+            cp.anchor[3 * i + 1] = cen[1];
+            cp.anchor[3 * i + 2] = cen[2];
         }
     }
+    return valid;
 }
+
+// the cell must stay inside the minimum-image range of every other seed: radius of
+// the polytope about the seed (at -z in the polytope's frame) against half the box
+template <typename R>
+__device__ __forceinline__ bool cell_too_large(const WarpPoly<R>& P, const CellCtx& cc,
+                                               float psimax_glob, float halfLmin, int lane) {
+    V3<R> z0;
+    z0.x = -(R)cc.fr.z[0];
+    z0.y = -(R)cc.fr.z[1];
+    z0.z = -(R)cc.fr.z[2];
+    float R0 = (float)poly_radius(P, z0, lane);
+    float dpsi = fmaxf(psimax_glob - cc.si.phi, 0.f);
+    return R0 + sqrtf(R0 * R0 + 2.f * dpsi) > halfLmin * 0.9999f;
+}
+
+// An FP32 cell whose centroid lies more than this many spacings from its frame
+// origin is clipped once more in a frame at the centroid (its rounding grows with the
+// distance of its vertices from the origin)
+constexpr float REFRAME_DIST = 0.5f;
 
 // clip by a list of seeds (warp-uniform count): each lane builds one plane, then the
 // warp clips by them in order
@@ -1191,12 +1276,17 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, 4)
         cc.si = load_seed(cp, i);
         bool bad = false;
         uint32_t st = 0;
+        float zprev[3] = {cp.anchor[3 * i], cp.anchor[3 * i + 1], cp.anchor[3 * i + 2]};
+        if (!(isfinite(zprev[0]) && isfinite(zprev[1]) && isfinite(zprev[2])))
+            zprev[0] = zprev[1] = zprev[2] = 0.f;
+        // FP32 cells: frame at the previous centroid; FP64 cells: at the seed
+        cc.fr = sizeof(R) == 4 ? make_frame(cp, zprev) : seed_frame();
 #ifdef SDOT_COUNTERS
         if (lane < 8) P.wc[lane] = 0;
         __syncwarp();
         WCOUNT(P, 6, 1);
 #endif
-        poly_init(P, cp, lane);
+        poly_init(P, cp, cc.fr.z, lane);
         // first candidates: the cell's facets in the previous diagram, then its k
         // nearest seeds
         int rc = CLIP_NONE;
@@ -1215,12 +1305,12 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, 4)
             rc = clip_list(P, cp, cc, cp.knn + i * cp.k, cp.k, lane, bad);
         if (rc == CLIP_EMPTY) st |= CS_EMPTY;
         if (rc == CLIP_CAP) st |= CS_CAPACITY | CS_CAP_POLY;
-        float zprev[3] = {cp.anchor[3 * i], cp.anchor[3 * i + 1], cp.anchor[3 * i + 2]};
-        if (!(isfinite(zprev[0]) && isfinite(zprev[1]) && isfinite(zprev[2])))
-            zprev[0] = zprev[1] = zprev[2] = 0.f;
         if (!st) {
             Bounds b;
-            for (int a = 0; a < 3; a++) b.yabs[a] = (float)cc.si.c[a] * cp.ht[a] + cc.si.off[a];
+            for (int a = 0; a < 3; a++) {
+                b.yabs[a] = (float)cc.si.c[a] * cp.ht[a] + cc.si.off[a];
+                b.zf[a] = cc.fr.z[a];
+            }
             b.psi_i = cc.si.phi;
             poly_bounds(P, cp, b, lane);
             bool done = true;
@@ -1242,15 +1332,34 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, 4)
                 continue;
             }
         }
-        if (!st) {
-            // the cell must stay inside the minimum-image range of every other seed
-            V3<R> z0;
-            z0.x = z0.y = z0.z = R(0);
-            float R0 = (float)poly_radius(P, z0, lane);
-            float dpsi = fmaxf(psimax_glob - cc.si.phi, 0.f);
-            if (R0 + sqrtf(R0 * R0 + 2.f * dpsi) > halfLmin * 0.9999f) st |= CS_TOO_LARGE;
+        if (!st && cell_too_large(P, cc, psimax_glob, halfLmin, lane)) st |= CS_TOO_LARGE;
+        float cen[3];
+        bool have_cen = false;
+        if (!(st & (CS_EMPTY | CS_CAPACITY)))
+            have_cen = integrate(P, cp, cc.fr, i, lane, bad, st, cen);
+        // FP32 cells far from their frame origin (the first diagram of a context, or a
+        // large step of psi): clip again by the facets just found, in a frame at the
+        // centroid just found. The facets are the cell's complete neighbour set, so no
+        // walk is needed; the outputs are overwritten.
+        if (sizeof(R) == 4 && have_cen && !(st & (CS_EMPTY | CS_CAPACITY | CS_TOO_LARGE))) {
+            float dz2 = 0.f;
+#pragma unroll
+            for (int a = 0; a < 3; a++) dz2 += (cen[a] - cc.fr.z[a]) * (cen[a] - cc.fr.z[a]);
+            if (dz2 > REFRAME_DIST * REFRAME_DIST) {
+                __syncwarp();  // facets and counts written by integrate
+                const int nf = min(cp.fcnt[i], FCAP);
+                __syncwarp();
+                cc.fr = make_frame(cp, cen);
+                bad = false;
+                st = 0;
+                poly_init(P, cp, cc.fr.z, lane);
+                int rc2 = clip_list(P, cp, cc, cp.fcol + i * FCAP, nf, lane, bad);
+                if (rc2 == CLIP_EMPTY) st |= CS_EMPTY;
+                if (rc2 == CLIP_CAP) st |= CS_CAPACITY | CS_CAP_POLY;
+                if (!st && cell_too_large(P, cc, psimax_glob, halfLmin, lane)) st |= CS_TOO_LARGE;
+                if (!(st & (CS_EMPTY | CS_CAPACITY))) integrate(P, cp, cc.fr, i, lane, bad, st, cen);
+            }
         }
-        if (!(st & (CS_EMPTY | CS_CAPACITY))) integrate(P, cp, i, lane, bad, st);
         if (bad) st |= CS_INCONSISTENT;
         if (lane == 0) {
             if (st & (CS_EMPTY | CS_CAPACITY)) {
