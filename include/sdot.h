@@ -44,13 +44,15 @@ enum {
     SDOT_ERR_EMPTY_CELL = -8, /* a Laguerre cell is empty at the given psi */
     SDOT_ERR_TIMEOUT = -9,    /* a bounded device wait gave up */
     SDOT_ERR_CUDA = -10,      /* CUDA runtime error */
-    SDOT_ERR_CAPACITY = -11   /* a cell exceeded the fixed polytope capacity even in FP64 */
+    SDOT_ERR_CAPACITY = -11,  /* a cell exceeded the fixed polytope capacity even in FP64 */
+    SDOT_ERR_NOT_READY = -12  /* a server job has not finished yet */
 };
 
 enum {
     SDOT_PREC_FP64 = 0,  /* clipping in FP64 */
-    SDOT_PREC_MIXED = 1  /* clipping in FP32 in seed-local coordinates, FP64 accumulation,
-                            FP64 re-clip of cells failing the consistency check */
+    SDOT_PREC_MIXED = 1  /* clipping in FP32 in a frame at each cell's previous centroid,
+                            FP64 plane offsets and accumulation, FP64 re-clip of cells
+                            failing the consistency check */
 };
 
 typedef struct {
@@ -210,6 +212,94 @@ int64_t sdot_kernel_launches(void);
 
 /* Message of the last error on the calling thread ("" if none). */
 const char* sdot_last_error(void);
+
+/*
+ * Reconstruction server: jobs of different N arrive at any time and run
+ * concurrently on one GPU. The paper states the problem for one box; serving many
+ * boxes is this library's addition.
+ *
+ * Admission: jobs wait in arrival order (FIFO, no overtaking) and are admitted while
+ * the sum of the admitted jobs' device footprints (sdot_server_footprint) stays
+ * within hbm_budget and at most max_active jobs are admitted. An admitted job keeps
+ * its whole state (positions, psi, kNN lists, facets, CSR Hessian, CG vectors)
+ * resident on the device until it finishes, then its memory and slot are released
+ * and the queue is admitted again. Each admitted job runs sdot_create, sdot_solve
+ * and sdot_displacement on a CUDA stream and host thread of its own, so the kernels
+ * of different jobs overlap on the device. A job's arithmetic does not depend on
+ * the other jobs: its results are the same alone and in any mix.
+ *
+ * Job states: SDOT_JOB_QUEUED, SDOT_JOB_RUNNING, SDOT_JOB_DONE, SDOT_JOB_FAILED.
+ * Times are seconds since sdot_server_create: arrival (submit), admission and
+ * completion; a job's latency is completion - arrival.
+ * The server functions are thread-safe.
+ */
+enum { SDOT_JOB_QUEUED = 0, SDOT_JOB_RUNNING = 1, SDOT_JOB_DONE = 2, SDOT_JOB_FAILED = 3 };
+
+typedef struct sdot_server sdot_server;
+
+typedef struct {
+    size_t hbm_budget; /* device bytes the admitted jobs may hold together; 0: 90% of the
+                          device memory free at creation */
+    int max_active;    /* jobs admitted at once (default 8) */
+    int device;        /* CUDA device ordinal; -1 (default): the current device */
+} sdot_server_options;
+
+typedef struct {
+    size_t hbm_budget, used_bytes, peak_used_bytes;
+    int max_active, active, peak_active;
+    int64_t queued, finished, submitted;
+} sdot_server_info;
+
+/* Fill *opt with the defaults listed in sdot_server_options. */
+int sdot_server_default_options(sdot_server_options* opt);
+
+/*
+ * Device bytes a job of N seeds in box holds while admitted (with options opt, NULL:
+ * defaults): every array sdot_create allocates, plus a reserve of 25 Hessian entries
+ * per seed (12 bytes each) for the CSR that sdot_solve builds. Host computation only.
+ */
+int sdot_server_footprint(int64_t N, const double box[3], const sdot_options* opt,
+                          size_t* bytes);
+
+/* Create a server (opt NULL: defaults). On error *out is NULL. */
+int sdot_server_create(const sdot_server_options* opt, sdot_server** out);
+
+/*
+ * Queue a job: the solve of sdot_create(pos, mass, N, box, opt) + sdot_solve(tol)
+ * + sdot_displacement. pos (N x 3) and mass (N, or NULL for uniform) must be host
+ * memory; they are copied before the call returns. *id receives the job's id.
+ * Returns SDOT_ERR_OOM if the job's footprint exceeds hbm_budget (it could never be
+ * admitted). Errors of the solve itself are reported by sdot_server_result.
+ */
+int sdot_server_submit(sdot_server* srv, const double* pos, const double* mass, int64_t N,
+                       const double box[3], const sdot_options* opt, double tol,
+                       int64_t* id);
+
+/* State of job id (*state: SDOT_JOB_*). */
+int sdot_server_poll(sdot_server* srv, int64_t id, int* state);
+
+/* Wait until job id has finished or timeout_s seconds passed (< 0: no limit);
+ * SDOT_ERR_TIMEOUT if it has not finished. *state (may be NULL) receives its state. */
+int sdot_server_wait(sdot_server* srv, int64_t id, double timeout_s, int* state);
+
+/*
+ * Collect a finished job and release its record. disp (N x 3) and psi (N) are host
+ * buffers in the job's seed order, or NULL; st (may be NULL) receives the solve's
+ * statistics; times (3 doubles, may be NULL) its arrival, admission and completion
+ * times. Returns the job's own result code (SDOT_OK or the error of its create or
+ * solve, whose message sdot_last_error() then gives on the calling thread), or
+ * SDOT_ERR_NOT_READY while it is queued or running (the record is kept). disp and psi
+ * are written only for a job that succeeded.
+ */
+int sdot_server_result(sdot_server* srv, int64_t id, double* disp, double* psi,
+                       sdot_stats* st, double times[3]);
+
+/* Occupancy and counters of the server. */
+int sdot_server_get_info(sdot_server* srv, sdot_server_info* info);
+
+/* Wait for the running jobs, drop the queued ones and release the server (NULL is
+ * accepted). */
+void sdot_server_destroy(sdot_server* srv);
 
 #ifdef __cplusplus
 }

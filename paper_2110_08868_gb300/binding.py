@@ -20,12 +20,13 @@ ERRORS = {
     -1: "SDOT_ERR_ARG", -2: "SDOT_ERR_MASS", -3: "SDOT_ERR_DUPLICATE", -4: "SDOT_ERR_TOO_FEW",
     -5: "SDOT_ERR_OOM", -6: "SDOT_ERR_NO_DESCENT", -7: "SDOT_ERR_MAXIT",
     -8: "SDOT_ERR_EMPTY_CELL", -9: "SDOT_ERR_TIMEOUT", -10: "SDOT_ERR_CUDA",
-    -11: "SDOT_ERR_CAPACITY",
+    -11: "SDOT_ERR_CAPACITY", -12: "SDOT_ERR_NOT_READY",
 }
 for _v, _n in ERRORS.items():
     globals()[_n] = _v
 SDOT_PREC_FP64 = 0
 SDOT_PREC_MIXED = 1
+SDOT_JOB_QUEUED, SDOT_JOB_RUNNING, SDOT_JOB_DONE, SDOT_JOB_FAILED = 0, 1, 2, 3
 
 
 class sdot_options(ctypes.Structure):
@@ -58,11 +59,31 @@ class sdot_stats(ctypes.Structure):
         return d
 
 
+class sdot_server_options(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_active", ctypes.c_int),
+                ("device", ctypes.c_int)]
+
+
+class sdot_server_info(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("used_bytes", ctypes.c_size_t),
+                ("peak_used_bytes", ctypes.c_size_t), ("max_active", ctypes.c_int),
+                ("active", ctypes.c_int), ("peak_active", ctypes.c_int),
+                ("queued", ctypes.c_int64), ("finished", ctypes.c_int64),
+                ("submitted", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 # every symbol include/sdot.h declares
 EXPORTS = ["sdot_default_options", "sdot_create", "sdot_set_stream", "sdot_laguerre",
            "sdot_solve", "sdot_csr_copy", "sdot_get_psi", "sdot_displacement", "sdot_knn",
            "sdot_cell_status", "sdot_knn_static", "sdot_size", "sdot_destroy",
-           "sdot_kernel_launches", "sdot_last_error"]
+           "sdot_kernel_launches", "sdot_last_error",
+           "sdot_server_default_options", "sdot_server_footprint", "sdot_server_create",
+           "sdot_server_submit", "sdot_server_poll", "sdot_server_wait", "sdot_server_result",
+           "sdot_server_get_info", "sdot_server_destroy"]
+_NO_STATUS = ("sdot_destroy", "sdot_last_error", "sdot_kernel_launches", "sdot_server_destroy")
 
 _lib = None
 
@@ -100,8 +121,20 @@ def load(path=LIB_PATH):
     lib.sdot_kernel_launches.restype = I64
     lib.sdot_last_error.argtypes = []
     lib.sdot_last_error.restype = ctypes.c_char_p
+    lib.sdot_server_default_options.argtypes = [ctypes.POINTER(sdot_server_options)]
+    lib.sdot_server_footprint.argtypes = [I64, P, ctypes.POINTER(sdot_options),
+                                          ctypes.POINTER(ctypes.c_size_t)]
+    lib.sdot_server_create.argtypes = [ctypes.POINTER(sdot_server_options), ctypes.POINTER(P)]
+    lib.sdot_server_submit.argtypes = [P, P, P, I64, P, ctypes.POINTER(sdot_options), D,
+                                       ctypes.POINTER(I64)]
+    lib.sdot_server_poll.argtypes = [P, I64, ctypes.POINTER(I)]
+    lib.sdot_server_wait.argtypes = [P, I64, D, ctypes.POINTER(I)]
+    lib.sdot_server_result.argtypes = [P, I64, P, P, ctypes.POINTER(sdot_stats), P]
+    lib.sdot_server_get_info.argtypes = [P, ctypes.POINTER(sdot_server_info)]
+    lib.sdot_server_destroy.argtypes = [P]
+    lib.sdot_server_destroy.restype = None
     for name in EXPORTS:
-        if name not in ("sdot_destroy", "sdot_last_error", "sdot_kernel_launches"):
+        if name not in _NO_STATUS:
             getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -288,3 +321,136 @@ def csr_to_scipy(h):
     val = np.empty(h.nnz, dtype=np.float64)
     check(sdot_csr_copy(h, rp, col, val))
     return sp.csr_matrix((val, col, rp), shape=(h.n, h.n))
+
+
+# ---------------------------------------------------------------------------
+# reconstruction server
+# ---------------------------------------------------------------------------
+def _box3(box):
+    return np.ascontiguousarray(np.broadcast_to(np.asarray(box, dtype=np.float64), (3,)))
+
+
+def sdot_server_default_options(**kw):
+    o = sdot_server_options()
+    load().sdot_server_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def sdot_server_footprint(n, box, opt=None):
+    """Returns (rc, bytes): device bytes a job of n seeds holds while admitted."""
+    b = _box3(box)
+    out = ctypes.c_size_t()
+    rc = load().sdot_server_footprint(int(n), ctypes.c_void_p(b.ctypes.data),
+                                      ctypes.byref(opt) if opt is not None else None,
+                                      ctypes.byref(out))
+    return rc, int(out.value)
+
+
+def sdot_server_create(opt=None):
+    """Returns (rc, srv)."""
+    srv = ctypes.c_void_p()
+    rc = load().sdot_server_create(ctypes.byref(opt) if opt is not None else None,
+                                   ctypes.byref(srv))
+    return rc, srv
+
+
+def sdot_server_submit(srv, pos, mass, box, tol, opt=None):
+    """Returns (rc, id). pos: N x 3 float64 numpy (host); mass: N float64 or None."""
+    b = _box3(box)
+    jid = ctypes.c_int64()
+    rc = load().sdot_server_submit(srv, _ptr(pos), _ptr(mass), int(pos.shape[0]),
+                                   ctypes.c_void_p(b.ctypes.data),
+                                   ctypes.byref(opt) if opt is not None else None, float(tol),
+                                   ctypes.byref(jid))
+    return rc, int(jid.value)
+
+
+def sdot_server_poll(srv, jid):
+    st = ctypes.c_int()
+    rc = load().sdot_server_poll(srv, int(jid), ctypes.byref(st))
+    return rc, st.value
+
+
+def sdot_server_wait(srv, jid, timeout_s=-1.0):
+    st = ctypes.c_int(-1)
+    rc = load().sdot_server_wait(srv, int(jid), float(timeout_s), ctypes.byref(st))
+    return rc, st.value
+
+
+def sdot_server_result(srv, jid, disp=None, psi=None, stats=None, times=None):
+    """disp (N x 3), psi (N), times (3): float64 numpy arrays or None."""
+    return load().sdot_server_result(srv, int(jid), _ptr(disp), _ptr(psi),
+                                     ctypes.byref(stats) if stats is not None else None,
+                                     _ptr(times))
+
+
+def sdot_server_get_info(srv):
+    info = sdot_server_info()
+    rc = load().sdot_server_get_info(srv, ctypes.byref(info))
+    return rc, info
+
+
+def sdot_server_destroy(srv):
+    if srv:
+        load().sdot_server_destroy(srv)
+
+
+class Server:
+    """Owning wrapper over one reconstruction server (raises on errors)."""
+
+    def __init__(self, hbm_budget=0, max_active=8, device=-1):
+        rc, self.srv = sdot_server_create(sdot_server_default_options(
+            hbm_budget=int(hbm_budget), max_active=int(max_active), device=int(device)))
+        check(rc)
+        self._n = {}
+
+    def submit(self, pos, box, tol, mass=None, **opts):
+        pos = np.ascontiguousarray(pos, dtype=np.float64)
+        rc, jid = sdot_server_submit(self.srv, pos, mass, box, tol, sdot_default_options(**opts))
+        check(rc)
+        self._n[jid] = int(pos.shape[0])
+        return jid
+
+    def state(self, jid):
+        rc, st = sdot_server_poll(self.srv, jid)
+        check(rc)
+        return st
+
+    def wait(self, jid, timeout_s=-1.0):
+        """True when the job finished within timeout_s seconds."""
+        rc, _ = sdot_server_wait(self.srv, jid, timeout_s)
+        if rc == SDOT_ERR_TIMEOUT:
+            return False
+        check(rc)
+        return True
+
+    def result(self, jid):
+        """dict(disp, psi, stats, times) of a finished job; raises on its error."""
+        n = self._n[jid]
+        disp = np.empty((n, 3))
+        psi = np.empty(n)
+        st = sdot_stats()
+        times = np.empty(3)
+        rc = sdot_server_result(self.srv, jid, disp, psi, st, times)
+        if rc != SDOT_ERR_NOT_READY:
+            self._n.pop(jid, None)
+        check(rc)
+        return dict(disp=disp, psi=psi, stats=st.as_dict(), times=times)
+
+    def info(self):
+        rc, info = sdot_server_get_info(self.srv)
+        check(rc)
+        return info.as_dict()
+
+    def close(self):
+        if self.srv:
+            sdot_server_destroy(self.srv)
+            self.srv = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsdot.so")
-SOURCES = ["grid_knn.cu", "clip.cu", "linalg.cu", "api.cu", "static_knn.cu"]
+SOURCES = ["grid_knn.cu", "clip.cu", "linalg.cu", "api.cu", "static_knn.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -41,7 +41,8 @@ def _stale(out, deps):
 
 def build(verbose=False, force=False, extra=()):
     os.makedirs(BUILD, exist_ok=True)
-    hdrs = [os.path.join(CSRC, "internal.cuh"), os.path.join(INCLUDE, "sdot.h")]
+    hdrs = [os.path.join(CSRC, "internal.cuh"), os.path.join(CSRC, "serve_sched.h"),
+            os.path.join(INCLUDE, "sdot.h")]
     objs = []
     jobs = []
     for src in SOURCES:

@@ -37,6 +37,8 @@ struct sdot_ctx {
     bool eval_valid = false;  // last evaluation is at d.psi
     float ms_knn = 0;
     EvalResult last{};
+    bool dry = false;         // allocation plan only: count bytes, allocate nothing
+    size_t bytes = 0;         // device bytes requested by the allocations so far
 };
 
 namespace {
@@ -44,6 +46,8 @@ namespace {
 int dev_alloc(sdot_ctx* c, void** p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
+    c->bytes += (bytes + 511) / 512 * 512;
+    if (c->dry) return SDOT_OK;
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -151,6 +155,66 @@ int build_csr(sdot_ctx* c) {
     return SDOT_OK;
 }
 
+// Every device array of a context for d.N seeds in box d.L (the hash grid, kNN lists,
+// facet slab, PCG vectors, psi pyramid, temp). With c->dry set nothing is allocated
+// and c->bytes receives the total, which is the footprint of a server job.
+int alloc_context(sdot_ctx* c) {
+    DeviceState& d = c->d;
+    const int64_t N = d.N;
+    const double boxvol = d.L[0] * d.L[1] * d.L[2];
+    int rc = SDOT_OK;
+    // grid dimensions (to size the temp buffer)
+    double h = cbrt(c->opt.seeds_per_leaf * boxvol / (double)N);
+    int64_t ncell = 1;
+    int G[3];
+    for (int a = 0; a < 3; a++) {
+        double g = floor(d.L[a] / h);
+        if (g < 1) g = 1;
+        if (g > 1024) g = 1024;
+        G[a] = (int)g;
+        ncell *= G[a];
+    }
+    if ((rc = alloc_n(c, &d.pos, N)) || (rc = alloc_n(c, &d.posf, N)) || (rc = alloc_n(c, &d.pslo, N)) || (rc = alloc_n(c, &d.ioff, N)) ||
+        (rc = alloc_n(c, &d.leafc, N)) ||
+        (rc = alloc_n(c, &d.perm, N)) || (rc = alloc_n(c, &d.iperm, N)) ||
+        (rc = alloc_n(c, &d.nu, N)) || (rc = alloc_n(c, &d.psi, N)) ||
+        (rc = alloc_n(c, &d.psi_trial, N)) || (rc = alloc_n(c, &d.knn, N * d.k)) ||
+        (rc = alloc_n(c, &d.knn_d2k, N)) || (rc = alloc_n(c, &d.vol, N)) ||
+        (rc = alloc_n(c, &d.m1, N * 3)) || (rc = alloc_n(c, &d.anchor, N * 3)) ||
+        (rc = alloc_n(c, &d.status, N)) || (rc = alloc_n(c, &d.fcnt, N)) ||
+        (rc = alloc_n(c, &d.fcol, N * FCAP)) || (rc = alloc_n(c, &d.fval, N * FCAP)) ||
+        (rc = alloc_n(c, &d.queue, N)) || (rc = alloc_n(c, &d.queue64, N)) ||
+        (rc = alloc_n(c, &d.counters, 32)) || (rc = alloc_n(c, &d.row_ptr, N + 1)) ||
+        (rc = alloc_n(c, &d.rowcnt, N + 1)) || (rc = alloc_n(c, &d.x, N)) ||
+        (rc = alloc_n(c, &d.r, N)) || (rc = alloc_n(c, &d.z, N)) || (rc = alloc_n(c, &d.p, N)) ||
+        (rc = alloc_n(c, &d.q, N)) || (rc = alloc_n(c, &d.dinv, N)) ||
+        (rc = alloc_n(c, &d.partials, 1 << 20)) || (rc = alloc_n(c, &d.scal, 64)) ||
+        (rc = alloc_n(c, &d.grid.cell_start, ncell + 1)) || (rc = alloc_n(c, &c->stage, N * 3)))
+        return rc;
+    d.delta = d.x;
+    size_t tb = (size_t)(((N * 4 + 255) / 256) * 256) + 2 * (size_t)(((ncell * 4 + 255) / 256) * 256) +
+                256 + scan_temp_bytes(ncell + 1) + 4096;
+    if ((rc = dev_alloc(c, &c->temp, tb))) return rc;
+    c->temp_bytes = tb;
+    // pyramid of psi bounds: level 0 = grid cells, each level 4x coarser, top <= 4^3
+    {
+        Pyramid& P = d.pyr;
+        int dim[3] = {G[0], G[1], G[2]};
+        int64_t off = 0;
+        P.nlev = 0;
+        while (true) {
+            for (int a = 0; a < 3; a++) P.dim[P.nlev][a] = dim[a];
+            P.off[P.nlev] = off;
+            off += (int64_t)dim[0] * dim[1] * dim[2];
+            P.nlev++;
+            if ((dim[0] <= 4 && dim[1] <= 4 && dim[2] <= 4) || P.nlev == MAXLEV) break;
+            for (int a = 0; a < 3; a++) dim[a] = (dim[a] + 3) / 4;
+        }
+        if ((rc = alloc_n(c, &P.psimax, off))) return rc;
+    }
+    return SDOT_OK;
+}
+
 void log_iter(const sdot_ctx* c, int it, const EvalResult& r, double alpha, int cg_it,
               double cg_res, int trials) {
     if (!c->opt.verbose) return;
@@ -167,48 +231,12 @@ void log_iter(const sdot_ctx* c, int it, const EvalResult& r, double alpha, int 
 
 }  // namespace
 
-extern "C" {
+namespace sdot {
 
-const char* sdot_last_error(void) { return g_err.c_str(); }
-
-int64_t sdot_kernel_launches(void) { return (int64_t)launch_count(); }
-
-int sdot_default_options(sdot_options* o) {
-    if (!o) return SDOT_ERR_ARG;
-    o->k = 24;
-    o->precision = SDOT_PREC_MIXED;
-    o->seeds_per_leaf = 2.0;
-    o->cg_rtol = 1e-3;
-    o->cg_maxit = 5000;
-    o->newton_maxit = 100;
-    o->alpha_min = 1.0 / (1 << 30);
-    o->verbose = 0;
-    o->warm_alpha = 1;
-    return SDOT_OK;
-}
-
-void sdot_destroy(sdot_ctx* c) {
-    if (!c) return;
-    for (void* p : c->allocs) cudaFree(p);
-    c->allocs.clear();
-    delete c;
-}
-
-int sdot_set_stream(sdot_ctx* c, void* stream) {
-    if (!c) return SDOT_ERR_ARG;
-    c->stream = (cudaStream_t)stream;
-    return SDOT_OK;
-}
-
-int sdot_size(const sdot_ctx* c, int64_t* N, int* k) {
-    if (!c) return SDOT_ERR_ARG;
-    if (N) *N = c->d.N;
-    if (k) *k = c->d.k;
-    return SDOT_OK;
-}
-
-int sdot_create(const double* pos, const double* mass, int64_t N, const double box[3],
-                const sdot_options* opt, sdot_ctx** out) {
+// sdot_create with all work on the given stream (the server creates each job's
+// context on a stream of its own)
+int create_context(const double* pos, const double* mass, int64_t N, const double box[3],
+                   const sdot_options* opt, cudaStream_t stream, sdot_ctx** out) {
     g_err.clear();
     if (!out) {
         set_error("sdot_create: out is NULL");
@@ -225,6 +253,7 @@ int sdot_create(const double* pos, const double* mass, int64_t N, const double b
             return SDOT_ERR_ARG;
         }
     sdot_ctx* c = new sdot_ctx();
+    c->stream = stream;
     sdot_default_options(&c->opt);
     if (opt) c->opt = *opt;
     if (check_opt(c->opt)) {
@@ -249,55 +278,7 @@ int sdot_create(const double* pos, const double* mass, int64_t N, const double b
         sdot_destroy(c);
         return code;
     };
-    // grid dimensions (to size the temp buffer)
-    double h = cbrt(c->opt.seeds_per_leaf * boxvol / (double)N);
-    int64_t ncell = 1;
-    int G[3];
-    for (int a = 0; a < 3; a++) {
-        double g = floor(box[a] / h);
-        if (g < 1) g = 1;
-        if (g > 1024) g = 1024;
-        G[a] = (int)g;
-        ncell *= G[a];
-    }
-    if ((rc = alloc_n(c, &d.pos, N)) || (rc = alloc_n(c, &d.posf, N)) || (rc = alloc_n(c, &d.pslo, N)) || (rc = alloc_n(c, &d.ioff, N)) ||
-        (rc = alloc_n(c, &d.leafc, N)) ||
-        (rc = alloc_n(c, &d.perm, N)) || (rc = alloc_n(c, &d.iperm, N)) ||
-        (rc = alloc_n(c, &d.nu, N)) || (rc = alloc_n(c, &d.psi, N)) ||
-        (rc = alloc_n(c, &d.psi_trial, N)) || (rc = alloc_n(c, &d.knn, N * d.k)) ||
-        (rc = alloc_n(c, &d.knn_d2k, N)) || (rc = alloc_n(c, &d.vol, N)) ||
-        (rc = alloc_n(c, &d.m1, N * 3)) || (rc = alloc_n(c, &d.anchor, N * 3)) ||
-        (rc = alloc_n(c, &d.status, N)) || (rc = alloc_n(c, &d.fcnt, N)) ||
-        (rc = alloc_n(c, &d.fcol, N * FCAP)) || (rc = alloc_n(c, &d.fval, N * FCAP)) ||
-        (rc = alloc_n(c, &d.queue, N)) || (rc = alloc_n(c, &d.queue64, N)) ||
-        (rc = alloc_n(c, &d.counters, 32)) || (rc = alloc_n(c, &d.row_ptr, N + 1)) ||
-        (rc = alloc_n(c, &d.rowcnt, N + 1)) || (rc = alloc_n(c, &d.x, N)) ||
-        (rc = alloc_n(c, &d.r, N)) || (rc = alloc_n(c, &d.z, N)) || (rc = alloc_n(c, &d.p, N)) ||
-        (rc = alloc_n(c, &d.q, N)) || (rc = alloc_n(c, &d.dinv, N)) ||
-        (rc = alloc_n(c, &d.partials, 1 << 20)) || (rc = alloc_n(c, &d.scal, 64)) ||
-        (rc = alloc_n(c, &d.grid.cell_start, ncell + 1)) || (rc = alloc_n(c, &c->stage, N * 3)))
-        return fail(rc);
-    d.delta = d.x;
-    size_t tb = (size_t)(((N * 4 + 255) / 256) * 256) + 2 * (size_t)(((ncell * 4 + 255) / 256) * 256) +
-                256 + scan_temp_bytes(ncell + 1) + 4096;
-    if ((rc = dev_alloc(c, &c->temp, tb))) return fail(rc);
-    c->temp_bytes = tb;
-    // pyramid of psi bounds: level 0 = grid cells, each level 4x coarser, top <= 4^3
-    {
-        Pyramid& P = d.pyr;
-        int dim[3] = {G[0], G[1], G[2]};
-        int64_t off = 0;
-        P.nlev = 0;
-        while (true) {
-            for (int a = 0; a < 3; a++) P.dim[P.nlev][a] = dim[a];
-            P.off[P.nlev] = off;
-            off += (int64_t)dim[0] * dim[1] * dim[2];
-            P.nlev++;
-            if ((dim[0] <= 4 && dim[1] <= 4 && dim[2] <= 4) || P.nlev == MAXLEV) break;
-            for (int a = 0; a < 3; a++) dim[a] = (dim[a] + 3) / 4;
-        }
-        if ((rc = alloc_n(c, &P.psimax, off))) return fail(rc);
-    }
+    if ((rc = alloc_context(c))) return fail(rc);
     cudaStream_t s = c->stream;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -355,6 +336,87 @@ int sdot_create(const double* pos, const double* mass, int64_t N, const double b
     }
     *out = c;
     return SDOT_OK;
+}
+
+// device bytes of a context for N seeds (the allocations of create_context, counted
+// without allocating) plus a reserve for the CSR Hessian of sdot_solve
+int context_footprint(int64_t N, const double box[3], const sdot_options* opt, size_t* bytes) {
+    if (!bytes || !box || N < 2 || N > (int64_t)INT32_MAX - 1) {
+        set_error("sdot_server_footprint: need box, bytes and 2 <= N < 2^31");
+        return SDOT_ERR_ARG;
+    }
+    for (int a = 0; a < 3; a++)
+        if (!(box[a] > 0) || !isfinite(box[a])) {
+            set_error("sdot_server_footprint: box lengths must be finite and positive");
+            return SDOT_ERR_ARG;
+        }
+    sdot_ctx c;
+    c.dry = true;
+    sdot_default_options(&c.opt);
+    if (opt) c.opt = *opt;
+    if (check_opt(c.opt) || c.opt.k > N - 1) {
+        set_error("sdot_server_footprint: invalid options (or k >= N)");
+        return SDOT_ERR_ARG;
+    }
+    DeviceState& d = c.d;
+    memset(&d, 0, sizeof d);
+    d.N = N;
+    d.k = c.opt.k;
+    for (int a = 0; a < 3; a++) d.L[a] = box[a];
+    d.a = cbrt(box[0] * box[1] * box[2] / (double)N);
+    int rc = alloc_context(&c);
+    if (rc) return rc;
+    // CSR: 25 entries per seed (int32 column + FP64 value), the capacity sdot_solve
+    // grows to on Zel'dovich boxes (about 17 nonzeros per row, 25% headroom)
+    *bytes = c.bytes + ((size_t)N * 25 * 12 + 511) / 512 * 512;
+    return SDOT_OK;
+}
+
+}  // namespace sdot
+
+extern "C" {
+
+const char* sdot_last_error(void) { return g_err.c_str(); }
+
+int64_t sdot_kernel_launches(void) { return (int64_t)launch_count(); }
+
+int sdot_default_options(sdot_options* o) {
+    if (!o) return SDOT_ERR_ARG;
+    o->k = 24;
+    o->precision = SDOT_PREC_MIXED;
+    o->seeds_per_leaf = 2.0;
+    o->cg_rtol = 1e-3;
+    o->cg_maxit = 5000;
+    o->newton_maxit = 100;
+    o->alpha_min = 1.0 / (1 << 30);
+    o->verbose = 0;
+    o->warm_alpha = 1;
+    return SDOT_OK;
+}
+
+void sdot_destroy(sdot_ctx* c) {
+    if (!c) return;
+    for (void* p : c->allocs) cudaFree(p);
+    c->allocs.clear();
+    delete c;
+}
+
+int sdot_set_stream(sdot_ctx* c, void* stream) {
+    if (!c) return SDOT_ERR_ARG;
+    c->stream = (cudaStream_t)stream;
+    return SDOT_OK;
+}
+
+int sdot_size(const sdot_ctx* c, int64_t* N, int* k) {
+    if (!c) return SDOT_ERR_ARG;
+    if (N) *N = c->d.N;
+    if (k) *k = c->d.k;
+    return SDOT_OK;
+}
+
+int sdot_create(const double* pos, const double* mass, int64_t N, const double box[3],
+                const sdot_options* opt, sdot_ctx** out) {
+    return create_context(pos, mass, N, box, opt, 0, out);
 }
 
 int sdot_laguerre(sdot_ctx* c, const double* psi, double* volumes, double* centroids,

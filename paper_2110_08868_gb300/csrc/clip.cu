@@ -1537,19 +1537,33 @@ __global__ void cell_reduce_final(const double* __restrict__ part, int nb, doubl
 
 template <typename R, int MODE>
 static int launch_clip(const ClipParams& cp, cudaStream_t s) {
-    static int blocks = 0;
     const size_t smem = sizeof(WarpPoly<R>) * WARPS_PER_BLOCK;
-    if (blocks == 0) {
-        SDOT_CUDA_TRY(cudaFuncSetAttribute(clip_kernel<R, MODE>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        SDOT_CUDA_TRY(cudaFuncSetAttribute(clip_kernel<R, MODE>,
-                                           cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    // kernel attributes and the persistent grid size, set once per instantiation
+    // (thread-safe: contexts of different host threads launch concurrently)
+    struct Setup {
+        int blocks;
+        cudaError_t err;
+    };
+    static const Setup setup = [smem] {
+        Setup u{0, cudaSuccess};
+        u.err = cudaFuncSetAttribute(clip_kernel<R, MODE>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (u.err == cudaSuccess)
+            u.err = cudaFuncSetAttribute(clip_kernel<R, MODE>,
+                                         cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, clip_kernel<R, MODE>,
-                                                      WARPS_PER_BLOCK * 32, smem);
+        if (u.err == cudaSuccess)
+            u.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, clip_kernel<R, MODE>,
+                                                                  WARPS_PER_BLOCK * 32, smem);
         if (per_sm < 1) per_sm = 1;
-        blocks = per_sm * num_sms();
+        u.blocks = per_sm * num_sms();
+        return u;
+    }();
+    if (setup.err != cudaSuccess) {
+        set_error(std::string("clip kernel setup: ") + cudaGetErrorString(setup.err));
+        return SDOT_ERR_CUDA;
     }
+    const int blocks = setup.blocks;
     int64_t need = (cp.nwork + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
     int nb = (int)(need < blocks ? need : blocks);
     if (nb < 1) return SDOT_OK;

@@ -23,14 +23,14 @@ static unsigned long long g_launches = 0;
 void note_launch() { __atomic_add_fetch(&g_launches, 1ull, __ATOMIC_RELAXED); }
 unsigned long long launch_count() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
+// SM count of the device current at the first call (initialised once, thread-safe)
 int num_sms() {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
+    static const int n = [] {
+        int dev = 0, m = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
+        cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, dev);
+        return m > 0 ? m : 1;
+    }();
     return n;
 }
 

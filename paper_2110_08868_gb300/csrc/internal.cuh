@@ -182,4 +182,10 @@ int centroids_user(const DeviceState& d, double* out_user, int wrap_abs, cudaStr
 int status_to_user(const DeviceState& d, uint8_t* out_user, cudaStream_t s);
 int check_masses(const DeviceState& d, double* sum_out, double* min_out, cudaStream_t s);
 
+// sdot_create with all work on stream (api.cu)
+int create_context(const double* pos, const double* mass, int64_t N, const double box[3],
+                   const sdot_options* opt, cudaStream_t stream, sdot_ctx** out);
+// device bytes a context for N seeds holds, CSR reserve included (api.cu)
+int context_footprint(int64_t N, const double box[3], const sdot_options* opt, size_t* bytes);
+
 }  // namespace sdot

@@ -30,6 +30,7 @@ __all__ = [
     "lattice",
     "CONFIGS",
     "make_config",
+    "serving_stream",
 ]
 
 
@@ -148,3 +149,18 @@ def make_config(n, L, spectrum, rms, seed, clumps=None):
         y = add_clumps(y, L, n, clumps["n_clumps"], clumps["n_extra"],
                        clumps["sigma"], seed + 100)
     return np.ascontiguousarray(y), uniform_masses(y.shape[0], L), float(L)
+
+
+def serving_stream(n_jobs=64, seed=4, lo=32, hi=128):
+    """The serving workload: job sizes and Poisson arrival gaps.
+
+    Job j is a periodic unit box of N_j = n_j^3 seeds, n_j = round(exp(U(ln lo, ln hi)))
+    (log-uniform in the side, hence in N), displaced by the 1/k spectrum at 0.3 lattice
+    spacings rms with seed 1000 + j. Returns (sides, gaps): gaps are the inter-arrival
+    times of a unit-rate Poisson process (gaps[0] = 0); divide them by the arrival rate.
+    """
+    rng = np.random.default_rng(seed)
+    sides = np.rint(np.exp(rng.uniform(np.log(lo), np.log(hi), n_jobs))).astype(int)
+    gaps = rng.standard_exponential(n_jobs)
+    gaps[0] = 0.0
+    return sides, gaps

@@ -1,0 +1,116 @@
+"""The reconstruction server on the GPU (through the C ABI).
+
+* Each job's result is the same alone and in a mix of concurrent jobs: bitwise, because
+  a job only runs its own context's kernels (integer atomics only, fixed-order
+  reductions), whatever else is on the device.
+* A job's result equals the direct single-box path (sdot_create + sdot_solve +
+  sdot_displacement) on the same input, bitwise.
+* Admission keeps the admitted jobs' footprints within the budget; a job larger than
+  the budget is refused; a job that fails reports its own error and leaves the others
+  intact.
+"""
+import numpy as np
+import pytest
+
+from paper_2110_08868_gb300 import ics
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2110_08868_gb300 import binding as B  # noqa: E402
+
+
+def _box(n, seed):
+    y, _, _ = ics.zeldovich_box(n, 1.0, ics.spectrum_kinv, 0.3, seed)
+    return np.ascontiguousarray(y)
+
+
+JOBS = [(12, 1001), (16, 1002), (20, 1003), (14, 1004)]
+TOL = 1e-6
+
+
+def _run(jobs, max_active, one_at_a_time):
+    srv = B.Server(max_active=max_active)
+    out = {}
+    try:
+        if one_at_a_time:
+            for n, seed in jobs:
+                jid = srv.submit(_box(n, seed), [1.0] * 3, TOL)
+                assert srv.wait(jid, 120.0)
+                out[(n, seed)] = srv.result(jid)
+        else:
+            ids = {(n, seed): srv.submit(_box(n, seed), [1.0] * 3, TOL) for n, seed in jobs}
+            for key, jid in ids.items():
+                assert srv.wait(jid, 120.0)
+                out[key] = srv.result(jid)
+        info = srv.info()
+    finally:
+        srv.close()
+    return out, info
+
+
+def test_same_alone_and_in_the_mix():
+    alone, _ = _run(JOBS, 1, True)
+    mixed, info = _run(JOBS, 8, False)
+    assert info["finished"] == len(JOBS)
+    for key in alone:
+        a, m = alone[key], mixed[key]
+        assert a["stats"]["max_rel_err"] <= TOL
+        np.testing.assert_array_equal(a["disp"], m["disp"])
+        np.testing.assert_array_equal(a["psi"], m["psi"])
+        assert a["stats"]["newton_iters"] == m["stats"]["newton_iters"]
+        assert a["stats"]["laguerre_evals"] == m["stats"]["laguerre_evals"]
+        t = m["times"]
+        assert t[0] <= t[1] <= t[2]
+
+
+def test_server_equals_direct_path():
+    n, seed = JOBS[2]
+    y = _box(n, seed)
+    s = B.Solver(y, [1.0] * 3)
+    st = s.solve(TOL)
+    d = s.displacement()
+    psi = s.psi()
+    srv = B.Server()
+    try:
+        jid = srv.submit(y, [1.0] * 3, TOL)
+        assert srv.wait(jid, 120.0)
+        r = srv.result(jid)
+    finally:
+        srv.close()
+    assert r["stats"]["newton_iters"] == st["newton_iters"]
+    np.testing.assert_array_equal(r["disp"], d)
+    np.testing.assert_array_equal(r["psi"], psi)
+
+
+def test_admission_budget_and_failures():
+    rc, fp_big = B.sdot_server_footprint(20 ** 3, [1.0] * 3)
+    B.check(rc)
+    budget = int(fp_big * 1.5)  # at most one 20^3 job at a time
+    srv = B.Server(hbm_budget=budget, max_active=8)
+    try:
+        # a job that can never fit
+        rc, _ = B.sdot_server_submit(srv.srv, _box(32, 7), None, [1.0] * 3, TOL,
+                                     B.sdot_default_options())
+        assert rc == B.SDOT_ERR_OOM
+        # a job that fails on the device side (duplicate seeds) among good ones
+        bad = _box(12, 8)
+        bad[5] = bad[9]
+        ids = [srv.submit(_box(20, 10 + t), [1.0] * 3, TOL) for t in range(3)]
+        jbad = srv.submit(bad, [1.0] * 3, TOL)
+        for jid in ids + [jbad]:
+            assert srv.wait(jid, 120.0)
+        with pytest.raises(B.SdotError) as e:
+            srv.result(jbad)
+        assert e.value.code == B.SDOT_ERR_DUPLICATE
+        for jid in ids:
+            assert srv.result(jid)["stats"]["max_rel_err"] <= TOL
+        info = srv.info()
+        assert info["peak_used_bytes"] <= budget
+        assert info["used_bytes"] == 0 and info["active"] == 0
+        assert info["finished"] == 4
+    finally:
+        srv.close()
