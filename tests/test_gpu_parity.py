@@ -213,3 +213,29 @@ def test_c2_sampled_cells_fp64():
     o = O.cells(y, np.zeros(N), L, "certified", idx=idx)
     np.testing.assert_allclose(g["vol"][idx], o["vol"], rtol=0, atol=1e-10 * a ** 3)
     assert abs(g["vol"].sum() - L ** 3) < 1e-9 * L ** 3
+
+
+def test_c3_sampled_cells_bench_box():
+    # the box bench.py times (256^3 lattice + 838 860 points in 2000 clumps of width
+    # 0.05a, 17.6 M seeds) at psi = 0, both precisions, in the default launch
+    # configuration: 2 lattice and 2 clump cells against the certified oracle
+    y, nu, L = ics.make_config(**ics.CONFIGS["zeldovich-256^3-kinv-0.3a+clumps"])
+    N = y.shape[0]
+    n_lat = 256 ** 3
+    a = L / 256
+    rng = np.random.default_rng(11)
+    idx = np.concatenate([rng.choice(n_lat, 2, replace=False),
+                          n_lat + rng.choice(N - n_lat, 2, replace=False)])
+    o = O.cells(y, np.zeros(N), L, "certified", idx=idx)
+    cen_o = y[idx] + o["m1"] / o["vol"][:, None]
+    for prec, vtol, ctol, stol in (("fp64", 1e-10, 1e-10, 1e-9), ("mixed", 2e-5, 2e-5, 1e-6)):
+        s = B.Solver(y, [L] * 3, precision=prec)
+        try:
+            g = s.laguerre()
+        finally:
+            s.close()
+        np.testing.assert_allclose(g["vol"][idx], o["vol"], rtol=0, atol=vtol * a ** 3)
+        dc = g["centroid"][idx] - cen_o
+        dc -= L * np.round(dc / L)
+        assert np.max(np.abs(dc)) <= ctol * a, (prec, np.max(np.abs(dc)) / a)
+        assert abs(g["vol"].sum() - L ** 3) < stol * L ** 3
