@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--rate", type=float, default=0.0,
                     help="arrivals per second (0: 1 / the mean solo solve time, calibrated)")
     ap.add_argument("--max-active", type=int, default=8)
+    ap.add_argument("--no-batch-clip", action="store_true",
+                    help="serving: each job launches its own clipping passes")
     return ap.parse_args()
 
 
@@ -408,7 +410,7 @@ def run_serving(args, rank, world, local):
     boxes = [np.ascontiguousarray(ics.zeldovich_box(int(n), 1.0, ics.spectrum_kinv, 0.3,
                                                     1000 + j)[0])
              for j, n in enumerate(sides)]
-    srv = B.Server(max_active=args.max_active)
+    srv = B.Server(max_active=args.max_active, batch_clip=not args.no_batch_clip)
     # warm-up and calibration: the solo solve time of a 64^3 job, scaled by N to the
     # stream's mean job size, sets the default arrival rate
     ycal = np.ascontiguousarray(ics.zeldovich_box(64, 1.0, ics.spectrum_kinv, 0.3, 999)[0])
@@ -462,6 +464,7 @@ def run_serving(args, rank, world, local):
                                    "arrivals",
                        "rate_per_s": rate, "calibration_solo_64^3_s": t_cal,
                        "tol": args.tol, "precision": "mixed", "max_active": args.max_active,
+                       "batch_clip": not args.no_batch_clip,
                        "hbm_budget": info["hbm_budget"], "total_cells": cells,
                        "l2": "each job's working set (>= 47 MB) and the mix exceed L2"},
             "e2e": {"value": p50, "unit": "s",

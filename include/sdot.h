@@ -225,8 +225,12 @@ const char* sdot_last_error(void);
  * resident on the device until it finishes, then its memory and slot are released
  * and the queue is admitted again. Each admitted job runs sdot_create, sdot_solve
  * and sdot_displacement on a CUDA stream and host thread of its own, so the kernels
- * of different jobs overlap on the device. A job's arithmetic does not depend on
- * the other jobs: its results are the same alone and in any mix.
+ * of different jobs overlap on the device. With batch_clip (default), the jobs'
+ * Laguerre evaluations are gathered by a batcher thread (it waits up to 0.2 ms for
+ * the other running jobs) and each clipping pass runs as one persistent launch
+ * over the cells of every job in the batch, pulled from one shared work counter.
+ * A job's arithmetic does not depend on the other jobs: its results are the same
+ * alone and in any mix.
  *
  * Job states: SDOT_JOB_QUEUED, SDOT_JOB_RUNNING, SDOT_JOB_DONE, SDOT_JOB_FAILED.
  * Times are seconds since sdot_server_create: arrival (submit), admission and
@@ -242,6 +246,9 @@ typedef struct {
                           device memory free at creation */
     int max_active;    /* jobs admitted at once (default 8) */
     int device;        /* CUDA device ordinal; -1 (default): the current device */
+    int batch_clip;    /* 1 (default): the running jobs' Laguerre evaluations are batched,
+                          each clipping pass one persistent launch over the cells of all
+                          of them; 0: each job launches its own passes */
 } sdot_server_options;
 
 typedef struct {

@@ -61,7 +61,7 @@ class sdot_stats(ctypes.Structure):
 
 class sdot_server_options(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_active", ctypes.c_int),
-                ("device", ctypes.c_int)]
+                ("device", ctypes.c_int), ("batch_clip", ctypes.c_int)]
 
 
 class sdot_server_info(ctypes.Structure):
@@ -400,9 +400,10 @@ def sdot_server_destroy(srv):
 class Server:
     """Owning wrapper over one reconstruction server (raises on errors)."""
 
-    def __init__(self, hbm_budget=0, max_active=8, device=-1):
+    def __init__(self, hbm_budget=0, max_active=8, device=-1, batch_clip=True):
         rc, self.srv = sdot_server_create(sdot_server_default_options(
-            hbm_budget=int(hbm_budget), max_active=int(max_active), device=int(device)))
+            hbm_budget=int(hbm_budget), max_active=int(max_active), device=int(device),
+            batch_clip=int(bool(batch_clip))))
         check(rc)
         self._n = {}
 

@@ -39,6 +39,8 @@ struct sdot_ctx {
     EvalResult last{};
     bool dry = false;         // allocation plan only: count bytes, allocate nothing
     size_t bytes = 0;         // device bytes requested by the allocations so far
+    EvalHook eval_hook = nullptr;  // the server's batcher, or null: evaluate_cells
+    void* eval_user = nullptr;
 };
 
 namespace {
@@ -106,8 +108,9 @@ int check_opt(const sdot_options& o) {
 }
 
 int eval_at(sdot_ctx* c, const double* psi_sorted, EvalResult* r, int precision = -1) {
-    int rc = evaluate_cells(c->d, psi_sorted, precision < 0 ? c->opt.precision : precision, r,
-                            c->stream);
+    const int prec = precision < 0 ? c->opt.precision : precision;
+    int rc = c->eval_hook ? c->eval_hook(c->eval_user, &c->d, psi_sorted, prec, r, c->stream)
+                          : evaluate_cells(c->d, psi_sorted, prec, r, c->stream);
     if (rc) return rc;
     return SDOT_OK;
 }
@@ -336,6 +339,11 @@ int create_context(const double* pos, const double* mass, int64_t N, const doubl
     }
     *out = c;
     return SDOT_OK;
+}
+
+void set_eval_hook(sdot_ctx* c, EvalHook hook, void* user) {
+    c->eval_hook = hook;
+    c->eval_user = user;
 }
 
 // device bytes of a context for N seeds (the allocations of create_context, counted

@@ -37,6 +37,9 @@
 #include <float.h>
 #include <math.h>
 
+#include <string>
+#include <vector>
+
 #include "internal.cuh"
 
 namespace sdot {
@@ -1246,6 +1249,133 @@ __device__ __noinline__ int clip_list(WarpPoly<R>& P, const ClipParams& cp, cons
     return CLIP_NONE;
 }
 
+// global upper bound of psi/a^2 (top pyramid level), every lane
+__device__ __forceinline__ float top_psimax(const ClipParams& cp, int lane) {
+    float m = -INFINITY;
+    const int tl = cp.pyr.nlev - 1;
+    const int ntop = cp.pyr.dim[tl][0] * cp.pyr.dim[tl][1] * cp.pyr.dim[tl][2];
+    for (int t = lane; t < ntop; t += 32) m = fmaxf(m, cp.pyr.psimax[cp.pyr.off[tl] + t]);
+    return warp_max(m);
+}
+
+// One work item w of a clipping pass: cell worklist[w] (or w), clipped by its first
+// candidates, certified (pass 1) or walked (re-queue pass), integrated; outputs
+// written, the cell queued for the next pass where needed.
+template <typename R, int MODE>
+__device__ __forceinline__ void process_cell(WarpPoly<R>& P, const ClipParams& cp, int64_t w,
+                                             float psimax_glob, float halfLmin, int lane) {
+    CellCtx cc;
+    cc.i = cp.worklist ? cp.worklist[w] : w;
+    const int64_t i = cc.i;
+    cc.yi = cp.pos[i];
+    cc.psii = cp.psi[i];
+    cc.si = load_seed(cp, i);
+    bool bad = false;
+    uint32_t st = 0;
+    float zprev[3] = {cp.anchor[3 * i], cp.anchor[3 * i + 1], cp.anchor[3 * i + 2]};
+    if (!(isfinite(zprev[0]) && isfinite(zprev[1]) && isfinite(zprev[2])))
+        zprev[0] = zprev[1] = zprev[2] = 0.f;
+    // FP32 cells: frame at the previous centroid; FP64 cells: at the seed
+    cc.fr = sizeof(R) == 4 ? make_frame(cp, zprev) : seed_frame();
+#ifdef SDOT_COUNTERS
+    if (lane < 8) P.wc[lane] = 0;
+    __syncwarp();
+    WCOUNT(P, 6, 1);
+#endif
+    poly_init(P, cp, cc.fr.z, lane);
+    // first candidates: the cell's facets in the previous diagram, then its k
+    // nearest seeds
+    int rc = CLIP_NONE;
+#ifdef SDOT_DIAG_NO_PREV
+    if (false) {
+#else
+    if (cp.facets_valid) {
+#endif
+        int nprev = min(cp.fcnt[i], FCAP);
+        rc = clip_list(P, cp, cc, cp.fcol + i * FCAP, nprev, lane, bad);
+    }
+    // the k nearest seeds start every cell of the first diagram, and any cell with
+    // no facets in the previous one
+    const bool use_knn = !cp.facets_valid || cp.fcnt[i] == 0;
+    if (use_knn && (rc == CLIP_NONE || rc == CLIP_CUT))
+        rc = clip_list(P, cp, cc, cp.knn + i * cp.k, cp.k, lane, bad);
+    if (rc == CLIP_EMPTY) st |= CS_EMPTY;
+    if (rc == CLIP_CAP) st |= CS_CAPACITY | CS_CAP_POLY;
+    if (!st) {
+        Bounds b;
+        for (int a = 0; a < 3; a++) {
+            b.yabs[a] = (float)cc.si.c[a] * cp.ht[a] + cc.si.off[a];
+            b.zf[a] = cc.fr.z[a];
+        }
+        b.psi_i = cc.si.phi;
+        poly_bounds(P, cp, b, lane);
+        bool done = true;
+        if (MODE == MODE_FULL) done = ring_walk(P, cp, cc, b, zprev, lane, bad, st);
+        if (done) done = traverse<R, MODE>(P, cp, cc, b, lane, bad, st);
+#ifdef SDOT_COUNTERS
+        __syncwarp();
+        if (lane < 8) atomicAdd(&cp.counters64[lane], (unsigned long long)P.wc[lane]);
+        __syncwarp();
+        if (lane < 8) P.wc[lane] = 0;
+        __syncwarp();
+#endif
+        if (!done && MODE == MODE_CERTIFY && (st & CS_UNCERTIFIED)) {
+            if (lane == 0) {
+                int32_t q = atomicAdd(cp.queue_cnt, 1);
+                cp.queue_out[q] = (int32_t)i;
+                cp.status[i] = (uint8_t)st;
+            }
+            return;
+        }
+    }
+    if (!st && cell_too_large(P, cc, psimax_glob, halfLmin, lane)) st |= CS_TOO_LARGE;
+    float cen[3];
+    bool have_cen = false;
+    if (!(st & (CS_EMPTY | CS_CAPACITY)))
+        have_cen = integrate(P, cp, cc.fr, i, lane, bad, st, cen);
+    // FP32 cells far from their frame origin (the first diagram of a context, or a
+    // large step of psi): clip again by the facets just found, in a frame at the
+    // centroid just found. The facets are the cell's complete neighbour set, so no
+    // walk is needed; the outputs are overwritten.
+    if (sizeof(R) == 4 && have_cen && !(st & (CS_EMPTY | CS_CAPACITY | CS_TOO_LARGE))) {
+        float dz2 = 0.f;
+#pragma unroll
+        for (int a = 0; a < 3; a++) dz2 += (cen[a] - cc.fr.z[a]) * (cen[a] - cc.fr.z[a]);
+        if (dz2 > REFRAME_DIST * REFRAME_DIST) {
+            __syncwarp();  // facets and counts written by integrate
+            const int nf = min(cp.fcnt[i], FCAP);
+            __syncwarp();
+            cc.fr = make_frame(cp, cen);
+            bad = false;
+            st = 0;
+            poly_init(P, cp, cc.fr.z, lane);
+            int rc2 = clip_list(P, cp, cc, cp.fcol + i * FCAP, nf, lane, bad);
+            if (rc2 == CLIP_EMPTY) st |= CS_EMPTY;
+            if (rc2 == CLIP_CAP) st |= CS_CAPACITY | CS_CAP_POLY;
+            if (!st && cell_too_large(P, cc, psimax_glob, halfLmin, lane)) st |= CS_TOO_LARGE;
+            if (!(st & (CS_EMPTY | CS_CAPACITY))) integrate(P, cp, cc.fr, i, lane, bad, st, cen);
+        }
+    }
+    if (bad) st |= CS_INCONSISTENT;
+    if (lane == 0) {
+        if (st & (CS_EMPTY | CS_CAPACITY)) {
+            // no facets from this cell (an empty cell has none; a cell over capacity
+            // is re-clipped or reported, and must not leave stale facet counts)
+            cp.fcnt[i] = 0;
+        }
+        if (st & CS_EMPTY) {
+            cp.vol[i] = 0.0;
+            cp.m1[3 * i] = cp.m1[3 * i + 1] = cp.m1[3 * i + 2] = 0.0;
+        }
+        cp.status[i] = (uint8_t)st;
+        bool redo = sizeof(R) == 4 && (st & (CS_INCONSISTENT | CS_CAPACITY));
+        if (redo) {
+            int32_t q = atomicAdd(cp.q64_cnt, 1);
+            cp.q64_out[q] = (int32_t)i;
+        }
+    }
+}
+
 template <typename R, int MODE>
 __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, 4)
     clip_kernel(ClipParams cp) {
@@ -1253,131 +1383,51 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, 4)
     WarpPoly<R>* polys = reinterpret_cast<WarpPoly<R>*>(smem_raw);
     const int lane = threadIdx.x & 31;
     WarpPoly<R>& P = polys[threadIdx.x >> 5];
-    // global upper bound of psi (top pyramid level)
-    float psimax_glob = -INFINITY;
-    {
-        int tl = cp.pyr.nlev - 1;
-        int ntop = cp.pyr.dim[tl][0] * cp.pyr.dim[tl][1] * cp.pyr.dim[tl][2];
-        for (int t = lane; t < ntop; t += 32)
-            psimax_glob = fmaxf(psimax_glob, cp.pyr.psimax[cp.pyr.off[tl] + t]);
-        psimax_glob = warp_max(psimax_glob);
-    }
+    const float psimax_glob = top_psimax(cp, lane);
     const float halfLmin = 0.5f * fminf(cp.Lt[0], fminf(cp.Lt[1], cp.Lt[2]));
     while (true) {
         int64_t w = 0;
         if (lane == 0) w = atomicAdd(cp.work_counter, 1);
         w = __shfl_sync(FULLMASK, w, 0);
         if (w >= cp.nwork) break;
-        CellCtx cc;
-        cc.i = cp.worklist ? cp.worklist[w] : w;
-        const int64_t i = cc.i;
-        cc.yi = cp.pos[i];
-        cc.psii = cp.psi[i];
-        cc.si = load_seed(cp, i);
-        bool bad = false;
-        uint32_t st = 0;
-        float zprev[3] = {cp.anchor[3 * i], cp.anchor[3 * i + 1], cp.anchor[3 * i + 2]};
-        if (!(isfinite(zprev[0]) && isfinite(zprev[1]) && isfinite(zprev[2])))
-            zprev[0] = zprev[1] = zprev[2] = 0.f;
-        // FP32 cells: frame at the previous centroid; FP64 cells: at the seed
-        cc.fr = sizeof(R) == 4 ? make_frame(cp, zprev) : seed_frame();
-#ifdef SDOT_COUNTERS
-        if (lane < 8) P.wc[lane] = 0;
-        __syncwarp();
-        WCOUNT(P, 6, 1);
-#endif
-        poly_init(P, cp, cc.fr.z, lane);
-        // first candidates: the cell's facets in the previous diagram, then its k
-        // nearest seeds
-        int rc = CLIP_NONE;
-#ifdef SDOT_DIAG_NO_PREV
-        if (false) {
-#else
-        if (cp.facets_valid) {
-#endif
-            int nprev = min(cp.fcnt[i], FCAP);
-            rc = clip_list(P, cp, cc, cp.fcol + i * FCAP, nprev, lane, bad);
+        process_cell<R, MODE>(P, cp, w, psimax_glob, halfLmin, lane);
+    }
+}
+
+// The same pass over the work items of several contexts in one persistent launch (a
+// batch of server jobs): item w of the batch belongs to the job j with
+// start[j] <= w < start[j + 1] and is that job's item w - start[j].
+struct ClipBatch {
+    const ClipParams* jobs;       // njobs entries, device memory
+    const int64_t* start;         // njobs + 1 prefix sums of the jobs' nwork
+    unsigned long long* counter;  // next batch item
+    int njobs;
+};
+
+template <typename R, int MODE>
+__global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, 4)
+    clip_batch_kernel(ClipBatch bt) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    WarpPoly<R>* polys = reinterpret_cast<WarpPoly<R>*>(smem_raw);
+    const int lane = threadIdx.x & 31;
+    WarpPoly<R>& P = polys[threadIdx.x >> 5];
+    const long long total = bt.start[bt.njobs];
+    while (true) {
+        long long w = 0;
+        if (lane == 0) w = (long long)atomicAdd(bt.counter, 1ull);
+        w = __shfl_sync(FULLMASK, w, 0);
+        if (w >= total) break;
+        // the last job j with start[j] <= w (jobs without items are skipped)
+        int lo = 0, hi = bt.njobs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (bt.start[mid] <= w) lo = mid;
+            else hi = mid - 1;
         }
-        // the k nearest seeds start every cell of the first diagram, and any cell with
-        // no facets in the previous one
-        const bool use_knn = !cp.facets_valid || cp.fcnt[i] == 0;
-        if (use_knn && (rc == CLIP_NONE || rc == CLIP_CUT))
-            rc = clip_list(P, cp, cc, cp.knn + i * cp.k, cp.k, lane, bad);
-        if (rc == CLIP_EMPTY) st |= CS_EMPTY;
-        if (rc == CLIP_CAP) st |= CS_CAPACITY | CS_CAP_POLY;
-        if (!st) {
-            Bounds b;
-            for (int a = 0; a < 3; a++) {
-                b.yabs[a] = (float)cc.si.c[a] * cp.ht[a] + cc.si.off[a];
-                b.zf[a] = cc.fr.z[a];
-            }
-            b.psi_i = cc.si.phi;
-            poly_bounds(P, cp, b, lane);
-            bool done = true;
-            if (MODE == MODE_FULL) done = ring_walk(P, cp, cc, b, zprev, lane, bad, st);
-            if (done) done = traverse<R, MODE>(P, cp, cc, b, lane, bad, st);
-#ifdef SDOT_COUNTERS
-            __syncwarp();
-            if (lane < 8) atomicAdd(&cp.counters64[lane], (unsigned long long)P.wc[lane]);
-            __syncwarp();
-            if (lane < 8) P.wc[lane] = 0;
-            __syncwarp();
-#endif
-            if (!done && MODE == MODE_CERTIFY && (st & CS_UNCERTIFIED)) {
-                if (lane == 0) {
-                    int32_t q = atomicAdd(cp.queue_cnt, 1);
-                    cp.queue_out[q] = (int32_t)i;
-                    cp.status[i] = (uint8_t)st;
-                }
-                continue;
-            }
-        }
-        if (!st && cell_too_large(P, cc, psimax_glob, halfLmin, lane)) st |= CS_TOO_LARGE;
-        float cen[3];
-        bool have_cen = false;
-        if (!(st & (CS_EMPTY | CS_CAPACITY)))
-            have_cen = integrate(P, cp, cc.fr, i, lane, bad, st, cen);
-        // FP32 cells far from their frame origin (the first diagram of a context, or a
-        // large step of psi): clip again by the facets just found, in a frame at the
-        // centroid just found. The facets are the cell's complete neighbour set, so no
-        // walk is needed; the outputs are overwritten.
-        if (sizeof(R) == 4 && have_cen && !(st & (CS_EMPTY | CS_CAPACITY | CS_TOO_LARGE))) {
-            float dz2 = 0.f;
-#pragma unroll
-            for (int a = 0; a < 3; a++) dz2 += (cen[a] - cc.fr.z[a]) * (cen[a] - cc.fr.z[a]);
-            if (dz2 > REFRAME_DIST * REFRAME_DIST) {
-                __syncwarp();  // facets and counts written by integrate
-                const int nf = min(cp.fcnt[i], FCAP);
-                __syncwarp();
-                cc.fr = make_frame(cp, cen);
-                bad = false;
-                st = 0;
-                poly_init(P, cp, cc.fr.z, lane);
-                int rc2 = clip_list(P, cp, cc, cp.fcol + i * FCAP, nf, lane, bad);
-                if (rc2 == CLIP_EMPTY) st |= CS_EMPTY;
-                if (rc2 == CLIP_CAP) st |= CS_CAPACITY | CS_CAP_POLY;
-                if (!st && cell_too_large(P, cc, psimax_glob, halfLmin, lane)) st |= CS_TOO_LARGE;
-                if (!(st & (CS_EMPTY | CS_CAPACITY))) integrate(P, cp, cc.fr, i, lane, bad, st, cen);
-            }
-        }
-        if (bad) st |= CS_INCONSISTENT;
-        if (lane == 0) {
-            if (st & (CS_EMPTY | CS_CAPACITY)) {
-                // no facets from this cell (an empty cell has none; a cell over capacity
-                // is re-clipped or reported, and must not leave stale facet counts)
-                cp.fcnt[i] = 0;
-            }
-            if (st & CS_EMPTY) {
-                cp.vol[i] = 0.0;
-                cp.m1[3 * i] = cp.m1[3 * i + 1] = cp.m1[3 * i + 2] = 0.0;
-            }
-            cp.status[i] = (uint8_t)st;
-            bool redo = sizeof(R) == 4 && (st & (CS_INCONSISTENT | CS_CAPACITY));
-            if (redo) {
-                int32_t q = atomicAdd(cp.q64_cnt, 1);
-                cp.q64_out[q] = (int32_t)i;
-            }
-        }
+        const ClipParams cp = bt.jobs[lo];
+        const float psimax_glob = top_psimax(cp, lane);
+        const float halfLmin = 0.5f * fminf(cp.Lt[0], fminf(cp.Lt[1], cp.Lt[2]));
+        process_cell<R, MODE>(P, cp, (int64_t)(w - bt.start[lo]), psimax_glob, halfLmin, lane);
     }
 }
 
@@ -1573,10 +1623,9 @@ static int launch_clip(const ClipParams& cp, cudaStream_t s) {
     return SDOT_OK;
 }
 
-int evaluate_cells(DeviceState& d, const double* psi, int precision, EvalResult* res,
-                   cudaStream_t s) {
-    int rc = build_pyramid(d, psi, s);
-    if (rc) return rc;
+// clipping parameters of one evaluation of context d at psi (no work counter,
+// work list or counters yet)
+static ClipParams make_clip_params(DeviceState& d, const double* psi) {
     ClipParams cp;
     cp.N = d.N;
     cp.k = d.k;
@@ -1614,6 +1663,18 @@ int evaluate_cells(DeviceState& d, const double* psi, int precision, EvalResult*
     cp.queue_cnt = d.counters + 0;
     cp.q64_out = d.queue64;
     cp.q64_cnt = d.counters + 1;
+    cp.counters64 = (unsigned long long*)(d.counters + 8);
+    cp.work_counter = nullptr;
+    cp.worklist = nullptr;
+    cp.nwork = d.N;
+    return cp;
+}
+
+int evaluate_cells(DeviceState& d, const double* psi, int precision, EvalResult* res,
+                   cudaStream_t s) {
+    int rc = build_pyramid(d, psi, s);
+    if (rc) return rc;
+    ClipParams cp = make_clip_params(d, psi);
     SDOT_CUDA_TRY(cudaMemsetAsync(d.counters, 0, 8 * sizeof(int32_t), s));
 
     cudaEvent_t e0, e1, ep1, ep2;
@@ -1687,6 +1748,262 @@ int evaluate_cells(DeviceState& d, const double* psi, int precision, EvalResult*
     res->requeued = requeued;
     res->reclipped = reclipped;
     res->ms = ms;
+    return SDOT_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// batched evaluation: one persistent launch per pass over the cells of several
+// contexts (the server's jobs)
+// ---------------------------------------------------------------------------
+template <typename R, int MODE>
+static int launch_clip_batch(const ClipBatch& bt, int64_t total, cudaStream_t s) {
+    const size_t smem = sizeof(WarpPoly<R>) * WARPS_PER_BLOCK;
+    struct Setup {
+        int blocks;
+        cudaError_t err;
+    };
+    static const Setup setup = [smem] {
+        Setup u{0, cudaSuccess};
+        u.err = cudaFuncSetAttribute(clip_batch_kernel<R, MODE>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (u.err == cudaSuccess)
+            u.err = cudaFuncSetAttribute(clip_batch_kernel<R, MODE>,
+                                         cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        int per_sm = 0;
+        if (u.err == cudaSuccess)
+            u.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, clip_batch_kernel<R, MODE>, WARPS_PER_BLOCK * 32, smem);
+        if (per_sm < 1) per_sm = 1;
+        u.blocks = per_sm * num_sms();
+        return u;
+    }();
+    if (setup.err != cudaSuccess) {
+        set_error(std::string("clip batch kernel setup: ") + cudaGetErrorString(setup.err));
+        return SDOT_ERR_CUDA;
+    }
+    const int64_t need = (total + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
+    const int nb = (int)(need < setup.blocks ? need : setup.blocks);
+    if (nb < 1) return SDOT_OK;
+    clip_batch_kernel<R, MODE><<<nb, WARPS_PER_BLOCK * 32, smem, s>>>(bt);
+    note_launch();
+    SDOT_CUDA_TRY(cudaGetLastError());
+    return SDOT_OK;
+}
+
+// Job tables of a batch: one slot per launch of a pass (the FP32 and the FP64 group);
+// the host copies are pinned and reused after the stream has been synchronised.
+struct BatchScratch {
+    int cap = 0;
+    ClipParams* jobs_dev[2] = {nullptr, nullptr};
+    int64_t* start_dev[2] = {nullptr, nullptr};
+    unsigned long long* counter_dev = nullptr;  // one per slot
+    ClipParams* jobs_host[2] = {nullptr, nullptr};
+    int64_t* start_host[2] = {nullptr, nullptr};
+    int32_t* cnt_host = nullptr;  // 2 per job: re-queued, FP64 re-clip counts
+    double* red_host = nullptr;   // 6 per job: the reductions of cell_reduce_final
+};
+
+void batch_scratch_destroy(BatchScratch* b) {
+    if (!b) return;
+    for (int t = 0; t < 2; t++) {
+        cudaFree(b->jobs_dev[t]);
+        cudaFree(b->start_dev[t]);
+        cudaFreeHost(b->jobs_host[t]);
+        cudaFreeHost(b->start_host[t]);
+    }
+    cudaFree(b->counter_dev);
+    cudaFreeHost(b->cnt_host);
+    cudaFreeHost(b->red_host);
+    delete b;
+}
+
+int batch_scratch_create(int cap, BatchScratch** out) {
+    *out = nullptr;
+    if (cap < 1) return SDOT_ERR_ARG;
+    BatchScratch* b = new BatchScratch();
+    b->cap = cap;
+    bool ok = true;
+    for (int t = 0; t < 2 && ok; t++) {
+        ok = cudaMalloc(&b->jobs_dev[t], sizeof(ClipParams) * cap) == cudaSuccess &&
+             cudaMalloc(&b->start_dev[t], sizeof(int64_t) * (cap + 1)) == cudaSuccess &&
+             cudaMallocHost(&b->jobs_host[t], sizeof(ClipParams) * cap) == cudaSuccess &&
+             cudaMallocHost(&b->start_host[t], sizeof(int64_t) * (cap + 1)) == cudaSuccess;
+    }
+    ok = ok && cudaMalloc(&b->counter_dev, sizeof(unsigned long long) * 2) == cudaSuccess &&
+         cudaMallocHost(&b->cnt_host, sizeof(int32_t) * 2 * cap) == cudaSuccess &&
+         cudaMallocHost(&b->red_host, sizeof(double) * 6 * cap) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        batch_scratch_destroy(b);
+        set_error("batch scratch: allocation failed");
+        return SDOT_ERR_OOM;
+    }
+    *out = b;
+    return SDOT_OK;
+}
+
+// one launch of pass MODE in precision R over the work items nwork[j] of the jobs with
+// take[j] (items: worklist of cps[j], or cells 0..nwork[j]-1)
+template <typename R, int MODE>
+static int launch_table(const std::vector<ClipParams>& cps, const std::vector<int64_t>& nwork,
+                        const std::vector<char>& take, int slot, BatchScratch* sc,
+                        cudaStream_t s) {
+    int m = 0;
+    int64_t total = 0;
+    ClipParams* hj = sc->jobs_host[slot];
+    int64_t* hs = sc->start_host[slot];
+    for (size_t j = 0; j < cps.size(); j++) {
+        if (!take[j] || nwork[j] <= 0) continue;
+        hj[m] = cps[j];
+        hj[m].nwork = nwork[j];
+        hj[m].work_counter = nullptr;  // the batch counter hands out the items
+        hs[m] = total;
+        total += nwork[j];
+        m++;
+    }
+    if (m == 0) return SDOT_OK;
+    hs[m] = total;
+    SDOT_CUDA_TRY(cudaMemcpyAsync(sc->jobs_dev[slot], hj, sizeof(ClipParams) * m,
+                                  cudaMemcpyHostToDevice, s));
+    SDOT_CUDA_TRY(cudaMemcpyAsync(sc->start_dev[slot], hs, sizeof(int64_t) * (m + 1),
+                                  cudaMemcpyHostToDevice, s));
+    SDOT_CUDA_TRY(cudaMemsetAsync(sc->counter_dev + slot, 0, sizeof(unsigned long long), s));
+    ClipBatch bt;
+    bt.jobs = sc->jobs_dev[slot];
+    bt.start = sc->start_dev[slot];
+    bt.counter = sc->counter_dev + slot;
+    bt.njobs = m;
+    return launch_clip_batch<R, MODE>(bt, total, s);
+}
+
+// the per-job counters (re-queued, FP64 re-clip) of every job, after a sync of s
+static int read_counts(DeviceState* const* ds, int n, BatchScratch* sc, cudaStream_t s) {
+    for (int j = 0; j < n; j++)
+        SDOT_CUDA_TRY(cudaMemcpyAsync(sc->cnt_host + 2 * j, ds[j]->counters, 2 * sizeof(int32_t),
+                                      cudaMemcpyDeviceToHost, s));
+    SDOT_CUDA_TRY(cudaStreamSynchronize(s));
+    return SDOT_OK;
+}
+
+int evaluate_cells_batch(DeviceState* const* ds, const double* const* psis, const int* precs,
+                         EvalResult* res, int n, BatchScratch* sc, cudaStream_t s) {
+    if (n < 1 || !sc || n > sc->cap) {
+        set_error("evaluate_cells_batch: batch size out of range");
+        return SDOT_ERR_ARG;
+    }
+    int rc;
+    std::vector<ClipParams> cps((size_t)n);
+    std::vector<int64_t> nwork((size_t)n);
+    std::vector<char> is64((size_t)n), is32((size_t)n), all((size_t)n, 1);
+    for (int j = 0; j < n; j++) {
+        DeviceState& d = *ds[j];
+        if ((rc = build_pyramid(d, psis[j], s))) return rc;
+        cps[j] = make_clip_params(d, psis[j]);
+        SDOT_CUDA_TRY(cudaMemsetAsync(d.counters, 0, 8 * sizeof(int32_t), s));
+        SDOT_CUDA_TRY(cudaMemsetAsync(d.counters + 8, 0, 64, s));
+        is64[j] = precs[j] == SDOT_PREC_FP64;
+        is32[j] = !is64[j];
+    }
+    cudaEvent_t e0, e1, ep1, ep2;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventCreate(&ep1);
+    cudaEventCreate(&ep2);
+    auto cleanup = [&] {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaEventDestroy(ep1);
+        cudaEventDestroy(ep2);
+    };
+    cudaEventRecord(e0, s);
+    // pass 1: every cell of every job
+    for (int j = 0; j < n; j++) {
+        cps[j].worklist = nullptr;
+        nwork[j] = ds[j]->N;
+    }
+    if ((rc = launch_table<float, MODE_CERTIFY>(cps, nwork, is32, 0, sc, s)) ||
+        (rc = launch_table<double, MODE_CERTIFY>(cps, nwork, is64, 1, sc, s))) {
+        cleanup();
+        return rc;
+    }
+    cudaEventRecord(ep1, s);
+    if ((rc = read_counts(ds, n, sc, s))) {
+        cleanup();
+        return rc;
+    }
+    std::vector<int64_t> requeued((size_t)n), reclipped((size_t)n);
+    bool any = false;
+    for (int j = 0; j < n; j++) {
+        requeued[j] = sc->cnt_host[2 * j];
+        cps[j].worklist = ds[j]->queue;
+        nwork[j] = requeued[j];
+        any = any || requeued[j] > 0;
+    }
+    // pass 2: the re-queued cells, full walk with clipping
+    if (any) {
+        if ((rc = launch_table<float, MODE_FULL>(cps, nwork, is32, 0, sc, s)) ||
+            (rc = launch_table<double, MODE_FULL>(cps, nwork, is64, 1, sc, s))) {
+            cleanup();
+            return rc;
+        }
+    }
+    cudaEventRecord(ep2, s);
+    if ((rc = read_counts(ds, n, sc, s))) {
+        cleanup();
+        return rc;
+    }
+    any = false;
+    for (int j = 0; j < n; j++) {
+        reclipped[j] = sc->cnt_host[2 * j + 1];
+        cps[j].worklist = ds[j]->queue64;
+        nwork[j] = is32[j] ? reclipped[j] : 0;
+        any = any || nwork[j] > 0;
+    }
+    // pass 3: FP64 re-clip of the FP32 jobs' cells that failed the FP32 checks
+    if (any && (rc = launch_table<double, MODE_FULL>(cps, nwork, all, 0, sc, s))) {
+        cleanup();
+        return rc;
+    }
+    cudaEventRecord(e1, s);
+    std::vector<unsigned long long> work((size_t)n * 8);
+    for (int j = 0; j < n; j++) {
+        DeviceState& d = *ds[j];
+        SDOT_CUDA_TRY(cudaMemcpyAsync(work.data() + 8 * j, d.counters + 8, 64,
+                                      cudaMemcpyDeviceToHost, s));
+        cell_reduce_kernel<<<RED_BLOCKS, 256, 0, s>>>(d.vol, d.nu, d.status, d.N, d.partials);
+        note_launch();
+        SDOT_CUDA_TRY(cudaGetLastError());
+        cell_reduce_final<<<1, 32, 0, s>>>(d.partials, RED_BLOCKS, d.scal);
+        note_launch();
+        SDOT_CUDA_TRY(cudaGetLastError());
+        SDOT_CUDA_TRY(cudaMemcpyAsync(sc->red_host + 6 * j, d.scal, 6 * sizeof(double),
+                                      cudaMemcpyDeviceToHost, s));
+    }
+    SDOT_CUDA_TRY(cudaStreamSynchronize(s));
+    float ms = 0, mp[3] = {0, 0, 0};
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventElapsedTime(&mp[0], e0, ep1);
+    cudaEventElapsedTime(&mp[1], ep1, ep2);
+    cudaEventElapsedTime(&mp[2], ep2, e1);
+    cleanup();
+    for (int j = 0; j < n; j++) {
+        DeviceState& d = *ds[j];
+        EvalResult& r = res[j];
+        const double* h = sc->red_host + 6 * j;
+        for (int q = 0; q < 8; q++) r.work[q] = work[8 * j + q];
+        d.facets_valid = 1;
+        r.sum_vol = h[0];
+        r.max_rel_err = h[1];
+        r.l2_err = h[2];
+        r.min_vol = h[3];
+        r.n_empty = (int64_t)h[4];
+        r.flags = (uint32_t)h[5];
+        r.requeued = requeued[j];
+        r.reclipped = reclipped[j];
+        r.ms = ms;
+        for (int q = 0; q < 3; q++) r.ms_pass[q] = mp[q];
+    }
     return SDOT_OK;
 }
 

@@ -164,6 +164,17 @@ struct EvalResult {
 int build_pyramid(DeviceState& d, const double* psi, cudaStream_t s);
 int evaluate_cells(DeviceState& d, const double* psi, int precision, EvalResult* res,
                    cudaStream_t s);
+// Batched evaluation of n contexts (one persistent launch per pass for all of their
+// cells; results identical to evaluate_cells on each context). The scratch holds the
+// job tables for up to cap contexts.
+struct BatchScratch;
+int batch_scratch_create(int cap, BatchScratch** out);
+void batch_scratch_destroy(BatchScratch* b);
+int evaluate_cells_batch(DeviceState* const* ds, const double* const* psis, const int* precs,
+                         EvalResult* res, int n, BatchScratch* sc, cudaStream_t s);
+// evaluation hook of a context (the server's batcher): replaces evaluate_cells
+typedef int (*EvalHook)(void* user, DeviceState* d, const double* psi, int precision,
+                        EvalResult* res, cudaStream_t s);
 
 // linalg.cu
 int csr_count(DeviceState& d, int64_t* nnz_out, cudaStream_t s);  // row_ptr and nnz
@@ -187,5 +198,7 @@ int create_context(const double* pos, const double* mass, int64_t N, const doubl
                    const sdot_options* opt, cudaStream_t stream, sdot_ctx** out);
 // device bytes a context for N seeds holds, CSR reserve included (api.cu)
 int context_footprint(int64_t N, const double box[3], const sdot_options* opt, size_t* bytes);
+// route the context's evaluations through hook (null: evaluate_cells) (api.cu)
+void set_eval_hook(sdot_ctx* c, EvalHook hook, void* user);
 
 }  // namespace sdot
