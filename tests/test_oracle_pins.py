@@ -73,6 +73,19 @@ def test_two_seed_slab(delta):
         assert abs(Lm[0, 0] - 4.0) < 1e-13
 
 
+@pytest.mark.parametrize("f", [0.3, 0.5, 0.62])
+def test_two_seed_unequal_masses_solve(f):
+    # masses (f, 1 - f) of the unit box for the slab pair above: V_1 = 1/2 + 4 delta must
+    # equal f, so psi_1 - psi_2 = (f - 1/2) / 4; cell 1 spans x in [-2 delta, 1/2 + 2 delta],
+    # symmetric about its seed (and cell 2 about its own), so both displacements vanish
+    y = np.array([[0.25, 0.5, 0.5], [0.75, 0.5, 0.5]])
+    psi, info = O.solve(y, np.array([f, 1.0 - f]), 1.0, tol=1e-13)
+    assert abs((psi[0] - psi[1]) - (f - 0.5) / 4) < 1e-13
+    assert abs(psi.sum()) < 1e-15
+    np.testing.assert_allclose(info["vol"], [f, 1.0 - f], rtol=0, atol=1e-13)
+    np.testing.assert_allclose(info["disp"], 0.0, atol=1e-13)
+
+
 def plane_wave(n, L, amps, phases):
     """Separable displacement s_a(q_a) = A_a sin(2 pi q_a / L + phi_a) and its exact psi.
 
