@@ -124,6 +124,18 @@ int sdot_create(const double* pos, const double* mass, int64_t N, const double b
 int sdot_set_stream(sdot_ctx* ctx, void* stream);
 
 /*
+ * Device allocator for the contexts created after this call (process-wide; both NULL
+ * restores cudaMalloc / cudaFree). alloc(bytes, user) returns device memory aligned to
+ * at least 256 bytes, or NULL, in which case the call that needed it fails with
+ * SDOT_ERR_OOM; free(ptr, user) releases a pointer alloc returned. A context keeps
+ * the allocator it was created with and frees through it. Give both functions or
+ * neither (else SDOT_ERR_ARG). The library's other device memory (the server's batch
+ * tables, the fixed array of sdot_knn_static) does not go through the allocator.
+ */
+int sdot_set_allocator(void* (*alloc)(size_t bytes, void* user),
+                       void (*free)(void* ptr, void* user), void* user);
+
+/*
  * One evaluation of the Laguerre diagram at psi (eq. laguerrecell) with the
  * quantities of eq. (SDK) and its derivatives.
  *  psi:       N doubles, or NULL for the context's current psi (0 after create).

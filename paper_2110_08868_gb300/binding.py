@@ -76,7 +76,8 @@ class sdot_server_info(ctypes.Structure):
 
 
 # every symbol include/sdot.h declares
-EXPORTS = ["sdot_default_options", "sdot_create", "sdot_set_stream", "sdot_laguerre",
+EXPORTS = ["sdot_default_options", "sdot_create", "sdot_set_stream", "sdot_set_allocator",
+           "sdot_laguerre",
            "sdot_solve", "sdot_csr_copy", "sdot_get_psi", "sdot_displacement", "sdot_knn",
            "sdot_cell_status", "sdot_knn_static", "sdot_size", "sdot_destroy",
            "sdot_kernel_launches", "sdot_last_error",
@@ -86,6 +87,11 @@ EXPORTS = ["sdot_default_options", "sdot_create", "sdot_set_stream", "sdot_lague
 _NO_STATUS = ("sdot_destroy", "sdot_last_error", "sdot_kernel_launches", "sdot_server_destroy")
 
 _lib = None
+
+# sdot_set_allocator callback types: alloc(bytes, user) -> ptr, free(ptr, user)
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+_allocator_refs = None  # keeps the installed callbacks alive
 
 
 class SdotError(RuntimeError):
@@ -106,6 +112,7 @@ def load(path=LIB_PATH):
     lib.sdot_default_options.argtypes = [ctypes.POINTER(sdot_options)]
     lib.sdot_create.argtypes = [P, P, I64, P, ctypes.POINTER(sdot_options), ctypes.POINTER(P)]
     lib.sdot_set_stream.argtypes = [P, P]
+    lib.sdot_set_allocator.argtypes = [ALLOC_FN, FREE_FN, P]
     lib.sdot_laguerre.argtypes = [P, P, P, P, ctypes.POINTER(sdot_csr)]
     lib.sdot_solve.argtypes = [P, D, P, ctypes.POINTER(sdot_stats)]
     lib.sdot_csr_copy.argtypes = [ctypes.POINTER(sdot_csr), P, P, P]
@@ -190,6 +197,18 @@ def sdot_create(pos, mass, box, opt=None):
     rc = lib.sdot_create(_ptr(pos), _ptr(mass), n, ctypes.c_void_p(b.ctypes.data),
                          ctypes.byref(opt) if opt is not None else None, ctypes.byref(ctx))
     return rc, ctx
+
+
+def sdot_set_allocator(alloc=None, free=None):
+    """Install Python callables alloc(bytes) -> device address (0: failure) and
+    free(ptr) for the contexts created later; no arguments restores cudaMalloc/cudaFree."""
+    global _allocator_refs
+    fa = ALLOC_FN(lambda n, u: alloc(n) or None) if alloc is not None else ALLOC_FN()
+    ff = FREE_FN(lambda p, u: free(p)) if free is not None else FREE_FN()
+    rc = load().sdot_set_allocator(fa, ff, None)
+    if rc == SDOT_OK:
+        _allocator_refs = (fa, ff) if alloc is not None else None
+    return rc
 
 
 def sdot_set_stream(ctx, stream):

@@ -11,6 +11,7 @@
 #include <string.h>
 
 #include <chrono>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -19,6 +20,15 @@
 namespace sdot {
 static thread_local std::string g_err;
 void set_error(const std::string& msg) { g_err = msg; }
+
+// device allocator of new contexts (sdot_set_allocator); null: cudaMalloc / cudaFree
+struct Allocator {
+    void* (*alloc)(size_t, void*) = nullptr;
+    void (*free)(void*, void*) = nullptr;
+    void* user = nullptr;
+};
+static std::mutex g_alloc_mu;
+static Allocator g_alloc;
 }  // namespace sdot
 
 using namespace sdot;
@@ -41,6 +51,7 @@ struct sdot_ctx {
     size_t bytes = 0;         // device bytes requested by the allocations so far
     EvalHook eval_hook = nullptr;  // the server's batcher, or null: evaluate_cells
     void* eval_user = nullptr;
+    Allocator alloc;               // the allocator at creation (frees with the same one)
 };
 
 namespace {
@@ -50,6 +61,16 @@ int dev_alloc(sdot_ctx* c, void** p, size_t bytes) {
     if (bytes == 0) bytes = 16;
     c->bytes += (bytes + 511) / 512 * 512;
     if (c->dry) return SDOT_OK;
+    if (c->alloc.alloc) {
+        *p = c->alloc.alloc(bytes, c->alloc.user);
+        if (!*p) {
+            set_error("device allocation of " + std::to_string(bytes) +
+                      " bytes failed (caller's allocator)");
+            return SDOT_ERR_OOM;
+        }
+        c->allocs.push_back(*p);
+        return SDOT_OK;
+    }
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -73,7 +94,8 @@ void dev_free(sdot_ctx* c, void* p) {
             c->allocs.erase(c->allocs.begin() + t);
             break;
         }
-    cudaFree(p);
+    if (c->alloc.free) c->alloc.free(p, c->alloc.user);
+    else cudaFree(p);
 }
 
 bool is_device_ptr(const void* p) {
@@ -257,6 +279,10 @@ int create_context(const double* pos, const double* mass, int64_t N, const doubl
         }
     sdot_ctx* c = new sdot_ctx();
     c->stream = stream;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        c->alloc = g_alloc;
+    }
     sdot_default_options(&c->opt);
     if (opt) c->opt = *opt;
     if (check_opt(c->opt)) {
@@ -404,9 +430,25 @@ int sdot_default_options(sdot_options* o) {
 
 void sdot_destroy(sdot_ctx* c) {
     if (!c) return;
-    for (void* p : c->allocs) cudaFree(p);
+    for (void* p : c->allocs) {
+        if (c->alloc.free) c->alloc.free(p, c->alloc.user);
+        else cudaFree(p);
+    }
     c->allocs.clear();
     delete c;
+}
+
+int sdot_set_allocator(void* (*alloc)(size_t, void*), void (*free_fn)(void*, void*), void* user) {
+    g_err.clear();
+    if ((alloc == nullptr) != (free_fn == nullptr)) {
+        set_error("sdot_set_allocator: give both alloc and free, or neither");
+        return SDOT_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc.alloc = alloc;
+    g_alloc.free = free_fn;
+    g_alloc.user = alloc ? user : nullptr;
+    return SDOT_OK;
 }
 
 int sdot_set_stream(sdot_ctx* c, void* stream) {

@@ -108,3 +108,51 @@ def test_error_codes_are_distinct_and_named():
     codes = [v for v in B.ERRORS]
     assert len(set(codes)) == len(codes) == 12
     assert sorted(codes) == list(range(-12, 0))
+
+
+def test_injected_allocator_failure_reports_oom():
+    # the caller's allocator refuses the first request: sdot_create stops there, frees
+    # nothing it did not get, and reports SDOT_ERR_OOM
+    calls = []
+
+    def alloc(n):
+        calls.append(n)
+        return 0
+
+    def free(p):
+        raise AssertionError("nothing was allocated")
+
+    assert B.sdot_set_allocator(alloc, free) == B.SDOT_OK
+    try:
+        rc, ctx = B.sdot_create(_pos(1000), None, [1.0] * 3)
+        assert rc == B.SDOT_ERR_OOM and not ctx.value
+        assert len(calls) == 1
+        assert "caller's allocator" in B.sdot_last_error()
+    finally:
+        assert B.sdot_set_allocator() == B.SDOT_OK
+
+
+def test_injected_allocator_partial_failure_frees_through_it():
+    # the allocator hands out 5 (never dereferenced) addresses, then fails: every
+    # address it gave is returned to it exactly once, none to cudaFree
+    given, freed = [], []
+
+    def alloc(n):
+        if len(given) == 5:
+            return 0
+        given.append(0x10000000 * (len(given) + 1))
+        return given[-1]
+
+    assert B.sdot_set_allocator(alloc, freed.append) == B.SDOT_OK
+    try:
+        rc, ctx = B.sdot_create(_pos(1000), None, [1.0] * 3)
+        assert rc == B.SDOT_ERR_OOM and not ctx.value
+        assert sorted(freed) == sorted(given) and len(given) == 5
+    finally:
+        assert B.sdot_set_allocator() == B.SDOT_OK
+
+
+def test_allocator_needs_both_functions():
+    assert B.sdot_set_allocator(alloc=lambda n: 0) == B.SDOT_ERR_ARG
+    assert B.sdot_set_allocator(free=lambda p: None) == B.SDOT_ERR_ARG
+    assert B.sdot_set_allocator() == B.SDOT_OK

@@ -124,23 +124,6 @@ def test_solve_fp64_matches_oracle_displacement():
     np.testing.assert_allclose(s.psi(), psi_o, atol=1e-7 * a * a)
 
 
-def test_solve_fp64_nonuniform_masses():
-    # per-seed masses (+-30%), normalised to the box volume: the masses enter through
-    # sdot_create in the caller's order
-    y, _, L = c1()
-    a = L / 16
-    N = y.shape[0]
-    w = 1.0 + 0.3 * np.random.default_rng(21).uniform(-1.0, 1.0, N)
-    nu = w / w.sum() * L ** 3
-    s = B.Solver(y, [L] * 3, mass=nu, precision="fp64")
-    st = s.solve(1e-10)
-    assert st["max_rel_err"] <= 1e-10
-    _, info = O.solve(y, nu, L, tol=1e-11)
-    assert np.max(np.abs(s.displacement() - info["disp"])) <= 1e-6 * a
-    g = s.laguerre(s.psi())
-    np.testing.assert_allclose(g["vol"], nu, rtol=1e-9)
-
-
 def test_solve_mixed_reaches_criterion():
     y, nu, L = c1()
     a = L / 16
@@ -256,3 +239,20 @@ def test_c3_sampled_cells_bench_box():
         dc -= L * np.round(dc / L)
         assert np.max(np.abs(dc)) <= ctol * a, (prec, np.max(np.abs(dc)) / a)
         assert abs(g["vol"].sum() - L ** 3) < stol * L ** 3
+
+
+def test_solve_fp64_nonuniform_masses():
+    # per-seed masses (+-30%), normalised to the box volume: the masses enter through
+    # sdot_create in the caller's order
+    y, _, L = c1()
+    a = L / 16
+    N = y.shape[0]
+    w = 1.0 + 0.3 * np.random.default_rng(21).uniform(-1.0, 1.0, N)
+    nu = w / w.sum() * L ** 3
+    s = B.Solver(y, [L] * 3, mass=nu, precision="fp64")
+    st = s.solve(1e-10)
+    assert st["max_rel_err"] <= 1e-10
+    _, info = O.solve(y, nu, L, tol=1e-11)
+    assert np.max(np.abs(s.displacement() - info["disp"])) <= 1e-6 * a
+    g = s.laguerre(s.psi())
+    np.testing.assert_allclose(g["vol"], nu, rtol=1e-9)
