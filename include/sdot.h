@@ -143,7 +143,8 @@ int sdot_set_allocator(void* (*alloc)(size_t bytes, void* user),
  *  volumes:   N doubles out (|V_j|) or NULL.
  *  centroids: N x 3 doubles out (absolute, wrapped into the box) or NULL.
  *  hess:      out, L = -Hessian(K) in the caller's index order, or NULL.
- * Returns SDOT_ERR_EMPTY_CELL (outputs still written) if some cell is empty.
+ * Returns SDOT_ERR_EMPTY_CELL (outputs still written) if some cell is empty, and
+ * SDOT_ERR_ARG (context unchanged) if psi has a non-finite entry.
  */
 int sdot_laguerre(sdot_ctx* ctx, const double* psi, double* volumes, double* centroids,
                   sdot_csr* hess);
@@ -159,7 +160,8 @@ int sdot_laguerre(sdot_ctx* ctx, const double* psi, double* volumes, double* cen
  * below 1e-3 and the full step alpha = 1 is rejected (FP32 rounding is the floor),
  * the current point is evaluated again with FP64 cells and the remaining Newton steps
  * stay FP64 (st->refined_fp64 = 1). The result keeps sum(psi) = 0.
- * st may be NULL.
+ * A psi0 with a non-finite entry is refused (SDOT_ERR_ARG) and leaves the context as
+ * it was. st may be NULL.
  */
 int sdot_solve(sdot_ctx* ctx, double tol, const double* psi0, sdot_stats* st);
 

@@ -479,7 +479,16 @@ int sdot_laguerre(sdot_ctx* c, const double* psi, double* volumes, double* centr
     if (psi) {
         const double* pv = nullptr;
         if ((rc = input_vec(c, psi, d.N, c->stage, &pv))) return rc;
-        if ((rc = gather_from_user(d, pv, d.psi, 1, s))) return rc;
+        // checked in the scratch vector first: a rejected psi leaves the context as it was
+        if ((rc = gather_from_user(d, pv, d.psi_trial, 1, s))) return rc;
+        bool ok = false;
+        if ((rc = all_finite(d, d.psi_trial, d.N, &ok, s))) return rc;
+        if (!ok) {
+            set_error("sdot_laguerre: psi has a non-finite entry");
+            return SDOT_ERR_ARG;
+        }
+        SDOT_CUDA_TRY(cudaMemcpyAsync(d.psi, d.psi_trial, (size_t)d.N * 8,
+                                      cudaMemcpyDeviceToDevice, s));
     }
     EvalResult r;
     if ((rc = eval_at(c, d.psi, &r))) return rc;
@@ -542,7 +551,16 @@ int sdot_solve(sdot_ctx* c, double tol, const double* psi0, sdot_stats* st) {
     if (psi0) {
         const double* pv = nullptr;
         if ((rc = input_vec(c, psi0, d.N, c->stage, &pv))) return rc;
-        if ((rc = gather_from_user(d, pv, d.psi, 1, s))) return rc;
+        // checked in the scratch vector first: a rejected psi0 leaves the context as it was
+        if ((rc = gather_from_user(d, pv, d.psi_trial, 1, s))) return rc;
+        bool ok = false;
+        if ((rc = all_finite(d, d.psi_trial, d.N, &ok, s))) return rc;
+        if (!ok) {
+            set_error("sdot_solve: psi0 has a non-finite entry");
+            return SDOT_ERR_ARG;
+        }
+        SDOT_CUDA_TRY(cudaMemcpyAsync(d.psi, d.psi_trial, (size_t)d.N * 8,
+                                      cudaMemcpyDeviceToDevice, s));
     } else {
         SDOT_CUDA_TRY(cudaMemsetAsync(d.psi, 0, (size_t)d.N * 8, s));
     }
@@ -573,7 +591,13 @@ int sdot_solve(sdot_ctx* c, double tol, const double* psi0, sdot_stats* st) {
     int prec = c->opt.precision;  // precision of the current evaluations
     rc = SDOT_OK;
     log_iter(c, it, ev, 0.0, 0, 0.0, 0);
-    while (ev.max_rel_err > tol) {
+    while (!(ev.max_rel_err <= tol)) {
+        if (!std::isfinite(ev.max_rel_err)) {
+            set_error("sdot_solve: non-finite cell volumes (psi far outside the range of "
+                      "the box geometry)");
+            rc = SDOT_ERR_ARG;
+            break;
+        }
         if (it >= c->opt.newton_maxit) {
             set_error("sdot_solve: Newton reached newton_maxit");
             rc = SDOT_ERR_MAXIT;

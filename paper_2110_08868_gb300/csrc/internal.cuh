@@ -192,6 +192,8 @@ int gather_from_user(const DeviceState& d, const double* user, double* sorted, i
 int centroids_user(const DeviceState& d, double* out_user, int wrap_abs, cudaStream_t s);
 int status_to_user(const DeviceState& d, uint8_t* out_user, cudaStream_t s);
 int check_masses(const DeviceState& d, double* sum_out, double* min_out, cudaStream_t s);
+// *ok = every v[i], i < n (device memory), is finite; synchronises s
+int all_finite(DeviceState& d, const double* v, int64_t n, bool* ok, cudaStream_t s);
 
 // sdot_create with all work on stream (api.cu)
 int create_context(const double* pos, const double* mass, int64_t N, const double box[3],

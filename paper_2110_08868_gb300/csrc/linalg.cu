@@ -518,6 +518,30 @@ __global__ void mass_kernel(const double* __restrict__ nu, int64_t N, double* __
     }
 }
 
+__global__ void nonfinite_kernel(const double* __restrict__ v, int64_t n,
+                                 int32_t* __restrict__ flag) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (!isfinite(v[i])) *flag = 1;  // every writer stores the same value
+}
+
+// *ok = every v[i], i < n (device memory), is finite; synchronises s
+int all_finite(DeviceState& d, const double* v, int64_t n, bool* ok, cudaStream_t s) {
+    int32_t* flag = d.counters + 24;
+    SDOT_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int32_t), s));
+    int64_t nb = (n + 255) / 256;
+    if (nb > 8 * num_sms()) nb = 8 * num_sms();
+    if (nb < 1) nb = 1;
+    nonfinite_kernel<<<(unsigned)nb, 256, 0, s>>>(v, n, flag);
+    note_launch();
+    SDOT_CUDA_TRY(cudaGetLastError());
+    int32_t h = 0;
+    SDOT_CUDA_TRY(cudaMemcpyAsync(&h, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    SDOT_CUDA_TRY(cudaStreamSynchronize(s));
+    *ok = h == 0;
+    return SDOT_OK;
+}
+
 int check_masses(const DeviceState& d, double* sum_out, double* min_out, cudaStream_t s) {
     const int nb = 64;
     mass_kernel<<<nb, 256, 0, s>>>(d.nu, d.N, d.partials);

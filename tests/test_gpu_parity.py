@@ -256,3 +256,22 @@ def test_solve_fp64_nonuniform_masses():
     assert np.max(np.abs(s.displacement() - info["disp"])) <= 1e-6 * a
     g = s.laguerre(s.psi())
     np.testing.assert_allclose(g["vol"], nu, rtol=1e-9)
+
+
+def test_fault_paths():
+    # non-finite psi is refused without touching the context; the Newton cap reports
+    y, nu, L = c1()
+    N = y.shape[0]
+    s = B.Solver(y, [L] * 3, precision="fp64")
+    bad = np.zeros(N)
+    bad[17] = np.nan
+    assert B.sdot_laguerre(s.ctx, bad, np.empty(N)) == B.SDOT_ERR_ARG
+    assert "non-finite" in B.sdot_last_error()
+    bad[17] = np.inf
+    assert B.sdot_solve(s.ctx, 1e-4, bad) == B.SDOT_ERR_ARG
+    st = s.solve(1e-8)
+    assert st["max_rel_err"] <= 1e-8
+    s.close()
+    s2 = B.Solver(y, [L] * 3, precision="fp64", newton_maxit=1)
+    assert B.sdot_solve(s2.ctx, 1e-12) == B.SDOT_ERR_MAXIT
+    s2.close()
