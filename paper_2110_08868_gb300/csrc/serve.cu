@@ -15,14 +15,9 @@
 // the other jobs in the batch.
 #include <string.h>
 
-#include <atomic>
 #include <chrono>
-#include <condition_variable>
-#include <deque>
 #include <memory>
-#include <mutex>
 #include <string>
-#include <thread>
 #include <vector>
 
 #include "internal.cuh"
@@ -47,130 +42,94 @@ constexpr int MAX_BATCH = 64;
 // how long the batcher waits for the other running jobs after the first request
 constexpr auto BATCH_WINDOW = std::chrono::microseconds(200);
 
-class Batcher {
-public:
-    explicit Batcher(int device) : device_(device) { th_ = std::thread(&Batcher::loop, this); }
+// one Laguerre evaluation asked for by a job's thread
+struct EvalReq {
+    DeviceState* d = nullptr;
+    const double* psi = nullptr;
+    int prec = 0;
+    EvalResult* r = nullptr;
+    int rc = SDOT_OK;
+    std::string err;
+};
 
-    ~Batcher() {
-        {
-            std::lock_guard<std::mutex> lk(mu_);
-            stop_ = true;
-        }
-        cv_.notify_all();
-        th_.join();
-    }
+// device state of the batcher's worker thread: its stream and job tables, made on
+// the first batch (on that thread) and released when the thread exits
+struct BatchDevice {
+    int device = 0;
+    bool ready = false;
+    int init_rc = SDOT_OK;
+    std::string init_err;
+    cudaStream_t s = nullptr;
+    BatchScratch* sc = nullptr;
 
-    void job_started() { active_++; }
-
-    void job_finished() {
-        active_--;
-        cv_.notify_all();
-    }
-
-    // Called by a job's thread (hook of its context): wait until the job's earlier work
-    // (and psi) is complete, queue the request, and wait for the batch result.
-    int evaluate(DeviceState* d, const double* psi, int prec, EvalResult* r,
-                 cudaStream_t job_stream) {
-        cudaError_t e = cudaStreamSynchronize(job_stream);
-        if (e != cudaSuccess) {
-            set_error(std::string("batched evaluation: ") + cudaGetErrorString(e));
-            return SDOT_ERR_CUDA;
-        }
-        Req q;
-        q.d = d;
-        q.psi = psi;
-        q.prec = prec;
-        q.r = r;
-        std::unique_lock<std::mutex> lk(mu_);
-        pending_.push_back(&q);
-        cv_.notify_all();
-        done_cv_.wait(lk, [&] { return q.done; });
-        if (q.rc != SDOT_OK) set_error(q.err);
-        return q.rc;
-    }
-
-    static int hook(void* user, DeviceState* d, const double* psi, int prec, EvalResult* r,
-                    cudaStream_t s) {
-        return static_cast<Batcher*>(user)->evaluate(d, psi, prec, r, s);
-    }
-
-private:
-    struct Req {
-        DeviceState* d = nullptr;
-        const double* psi = nullptr;
-        int prec = 0;
-        EvalResult* r = nullptr;
-        int rc = SDOT_OK;
-        bool done = false;
-        std::string err;
-    };
-
-    void loop() {
-        cudaStream_t s = nullptr;
-        BatchScratch* sc = nullptr;
-        int init_rc = SDOT_OK;
-        std::string init_err;
-        if (cudaSetDevice(device_) != cudaSuccess ||
+    void init() {
+        ready = true;
+        if (cudaSetDevice(device) != cudaSuccess ||
             cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
             init_rc = SDOT_ERR_CUDA;
             init_err = std::string("batcher: ") + cudaGetErrorString(cudaGetLastError());
-        } else if ((init_rc = batch_scratch_create(MAX_BATCH, &sc)) != SDOT_OK) {
+            return;
+        }
+        if ((init_rc = batch_scratch_create(MAX_BATCH, &sc)) != SDOT_OK)
             init_err = sdot_last_error();
-        }
-        std::unique_lock<std::mutex> lk(mu_);
-        while (true) {
-            cv_.wait(lk, [&] { return stop_ || !pending_.empty(); });
-            if (pending_.empty()) break;  // stop requested, nothing left
-            // give the other running jobs a short window to join this batch
-            cv_.wait_until(lk, std::chrono::steady_clock::now() + BATCH_WINDOW, [&] {
-                return stop_ || (int)pending_.size() >= active_.load();
-            });
-            std::vector<Req*> batch;
-            while (!pending_.empty() && (int)batch.size() < MAX_BATCH) {
-                batch.push_back(pending_.front());
-                pending_.pop_front();
-            }
-            lk.unlock();
-            int rc = init_rc;
-            std::string err = init_err;
-            if (rc == SDOT_OK) {
-                std::vector<DeviceState*> ds;
-                std::vector<const double*> psis;
-                std::vector<int> precs;
-                std::vector<EvalResult> res(batch.size());
-                for (Req* q : batch) {
-                    ds.push_back(q->d);
-                    psis.push_back(q->psi);
-                    precs.push_back(q->prec);
-                }
-                rc = evaluate_cells_batch(ds.data(), psis.data(), precs.data(), res.data(),
-                                          (int)batch.size(), sc, s);
-                if (rc == SDOT_OK)
-                    for (size_t t = 0; t < batch.size(); t++) *batch[t]->r = res[t];
-                else
-                    err = sdot_last_error();
-            }
-            lk.lock();
-            for (Req* q : batch) {
-                q->rc = rc;
-                q->err = err;
-                q->done = true;
-            }
-            done_cv_.notify_all();
-        }
-        lk.unlock();
-        batch_scratch_destroy(sc);
-        if (s) cudaStreamDestroy(s);
     }
 
-    const int device_;
-    std::thread th_;
-    std::mutex mu_;
-    std::condition_variable cv_, done_cv_;
-    std::deque<Req*> pending_;
-    std::atomic<int> active_{0};
-    bool stop_ = false;
+    void run(std::vector<EvalReq*>& reqs) {
+        if (!ready) init();
+        int rc = init_rc;
+        std::string err = init_err;
+        if (rc == SDOT_OK) {
+            std::vector<DeviceState*> ds;
+            std::vector<const double*> psis;
+            std::vector<int> precs;
+            std::vector<EvalResult> res(reqs.size());
+            for (EvalReq* q : reqs) {
+                ds.push_back(q->d);
+                psis.push_back(q->psi);
+                precs.push_back(q->prec);
+            }
+            rc = evaluate_cells_batch(ds.data(), psis.data(), precs.data(), res.data(),
+                                      (int)reqs.size(), sc, s);
+            if (rc == SDOT_OK)
+                for (size_t t = 0; t < reqs.size(); t++) *reqs[t]->r = res[t];
+            else
+                err = sdot_last_error();
+        }
+        for (EvalReq* q : reqs) {
+            q->rc = rc;
+            q->err = err;
+        }
+    }
+
+    void fini() {
+        batch_scratch_destroy(sc);
+        sc = nullptr;
+        if (s) cudaStreamDestroy(s);
+        s = nullptr;
+    }
 };
+
+using EvalBatcher = serve::Batcher<EvalReq>;
+
+// evaluation hook of a job's context: the job's earlier work (and psi) must be done
+// before the batcher's stream reads it, and the batcher's stream is synchronised
+// before the result comes back
+int batched_eval(void* user, DeviceState* d, const double* psi, int prec, EvalResult* r,
+                 cudaStream_t job_stream) {
+    cudaError_t e = cudaStreamSynchronize(job_stream);
+    if (e != cudaSuccess) {
+        set_error(std::string("batched evaluation: ") + cudaGetErrorString(e));
+        return SDOT_ERR_CUDA;
+    }
+    EvalReq q;
+    q.d = d;
+    q.psi = psi;
+    q.prec = prec;
+    q.r = r;
+    static_cast<EvalBatcher*>(user)->submit(&q);
+    if (q.rc != SDOT_OK) set_error(q.err);
+    return q.rc;
+}
 
 bool host_pointer(const void* p) {
     cudaPointerAttributes a;
@@ -183,7 +142,7 @@ bool host_pointer(const void* p) {
 
 // the device work of one job, on the calling worker thread (batcher: null for
 // unbatched evaluations)
-int run_job(int device, Batcher* batcher, JobPayload& j) {
+int run_job(int device, EvalBatcher* batcher, JobPayload& j) {
     if (cudaSetDevice(device) != cudaSuccess) {
         j.err = std::string("server job: cudaSetDevice: ") + cudaGetErrorString(cudaGetLastError());
         return SDOT_ERR_CUDA;
@@ -197,11 +156,11 @@ int run_job(int device, Batcher* batcher, JobPayload& j) {
     int rc = create_context(j.pos.data(), j.mass.empty() ? nullptr : j.mass.data(), j.N, j.box,
                             &j.opt, s, &ctx);
     if (rc == SDOT_OK && batcher) {
-        set_eval_hook(ctx, &Batcher::hook, batcher);
-        batcher->job_started();
+        set_eval_hook(ctx, &batched_eval, batcher);
+        batcher->add_active(1);
     }
     if (rc == SDOT_OK) rc = sdot_solve(ctx, j.tol, nullptr, &j.stats);
-    if (ctx && batcher) batcher->job_finished();
+    if (ctx && batcher) batcher->add_active(-1);
     if (rc == SDOT_OK) {
         j.disp.resize((size_t)j.N * 3);
         rc = sdot_displacement(ctx, j.disp.data());
@@ -229,8 +188,11 @@ using namespace sdot;
 
 struct sdot_server {
     int device = 0;
-    // declared before the scheduler: destroyed after it, once no job can wait on it
-    std::unique_ptr<Batcher> batcher;
+    // destroyed in reverse order: the scheduler first (no job can then wait on the
+    // batcher), then the batcher (its thread releases the batch device state), then
+    // that state
+    std::unique_ptr<BatchDevice> bdev;
+    std::unique_ptr<EvalBatcher> batcher;
     std::unique_ptr<serve::Scheduler<JobPayload>> sched;
 };
 
@@ -287,8 +249,15 @@ int sdot_server_create(const sdot_server_options* opt, sdot_server** out) {
     }
     sdot_server* srv = new sdot_server();
     srv->device = dev;
-    if (o.batch_clip) srv->batcher.reset(new Batcher(dev));
-    Batcher* bt = srv->batcher.get();
+    if (o.batch_clip) {
+        srv->bdev.reset(new BatchDevice());
+        srv->bdev->device = dev;
+        BatchDevice* bd = srv->bdev.get();
+        srv->batcher.reset(new EvalBatcher(
+            BATCH_WINDOW, MAX_BATCH, [bd](std::vector<EvalReq*>& reqs) { bd->run(reqs); },
+            [bd] { bd->fini(); }));
+    }
+    EvalBatcher* bt = srv->batcher.get();
     srv->sched.reset(new serve::Scheduler<JobPayload>(
         budget, o.max_active, [dev, bt](JobPayload& j) { return run_job(dev, bt, j); }));
     *out = srv;
@@ -381,6 +350,7 @@ void sdot_server_destroy(sdot_server* srv) {
     if (!srv) return;
     srv->sched.reset();  // waits for the running jobs, which may still use the batcher
     srv->batcher.reset();
+    srv->bdev.reset();
     delete srv;
 }
 

@@ -248,5 +248,113 @@ private:
     bool stopping_ = false;
 };
 
+// Gathers requests of concurrent callers into batches for one worker thread. A caller
+// blocks in submit() until the batch holding its request has run. The worker takes
+// the first pending request, waits up to `window` for more (or until as many are
+// pending as callers are active), hands up to max_batch requests to run_batch (which
+// fills in their results), and wakes their callers. fini runs on the worker thread
+// when it exits. The batch composition never changes what run_batch computes for a
+// request, only when it runs.
+template <class Req>
+class Batcher {
+public:
+    using RunFn = std::function<void(std::vector<Req*>&)>;
+    using FiniFn = std::function<void()>;
+
+    struct Stats {
+        int64_t batches, requests;
+        int max_batch_seen;
+    };
+
+    Batcher(std::chrono::microseconds window, int max_batch, RunFn run, FiniFn fini = nullptr)
+        : window_(window), max_batch_(max_batch < 1 ? 1 : max_batch), run_(std::move(run)),
+          fini_(std::move(fini)) {
+        th_ = std::thread(&Batcher::loop, this);
+    }
+
+    Batcher(const Batcher&) = delete;
+    Batcher& operator=(const Batcher&) = delete;
+
+    // Stops the worker; no caller may be inside submit() any more.
+    ~Batcher() {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        th_.join();
+    }
+
+    // callers that may submit soon (the window ends early once all of them wait)
+    void add_active(int delta) {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            active_ += delta;
+        }
+        cv_.notify_all();
+    }
+
+    void submit(Req* r) {
+        Slot q;
+        q.req = r;
+        std::unique_lock<std::mutex> lk(mu_);
+        pending_.push_back(&q);
+        cv_.notify_all();
+        done_cv_.wait(lk, [&] { return q.done; });
+    }
+
+    Stats stats() const {
+        std::lock_guard<std::mutex> lk(mu_);
+        return Stats{batches_, requests_, max_seen_};
+    }
+
+private:
+    struct Slot {
+        Req* req = nullptr;
+        bool done = false;
+    };
+
+    void loop() {
+        std::unique_lock<std::mutex> lk(mu_);
+        while (true) {
+            cv_.wait(lk, [&] { return stop_ || !pending_.empty(); });
+            if (pending_.empty()) break;  // stop requested, nothing left
+            cv_.wait_until(lk, std::chrono::steady_clock::now() + window_, [&] {
+                return stop_ || (int)pending_.size() >= active_;
+            });
+            std::vector<Slot*> slots;
+            while (!pending_.empty() && (int)slots.size() < max_batch_) {
+                slots.push_back(pending_.front());
+                pending_.pop_front();
+            }
+            lk.unlock();
+            std::vector<Req*> reqs;
+            for (Slot* q : slots) reqs.push_back(q->req);
+            run_(reqs);
+            lk.lock();
+            batches_++;
+            requests_ += (int64_t)slots.size();
+            if ((int)slots.size() > max_seen_) max_seen_ = (int)slots.size();
+            for (Slot* q : slots) q->done = true;
+            done_cv_.notify_all();
+        }
+        lk.unlock();
+        if (fini_) fini_();
+    }
+
+    const std::chrono::microseconds window_;
+    const int max_batch_;
+    RunFn run_;
+    FiniFn fini_;
+    std::thread th_;
+    mutable std::mutex mu_;
+    std::condition_variable cv_, done_cv_;
+    std::deque<Slot*> pending_;
+    int active_ = 0;
+    bool stop_ = false;
+    int64_t batches_ = 0, requests_ = 0;
+    int max_seen_ = 0;
+};
+
 }  // namespace serve
 }  // namespace sdot

@@ -12,6 +12,7 @@
 
 #include "serve_sched.h"
 
+using sdot::serve::Batcher;
 using sdot::serve::Scheduler;
 
 namespace {
@@ -189,6 +190,79 @@ int main() {
         auto f = s.info();
         check(ok.load() == 64 && f.finished == 64 && f.peak_used <= 50 && f.peak_active <= 4,
               "64 jobs from 8 threads");
+    }
+    // 9. batcher: every request gets its own result; concurrent requests share batches
+    {
+        struct R {
+            int in = 0, out = 0, batch = 0;
+        };
+        Batcher<R> b(std::chrono::microseconds(2000), 4, [](std::vector<R*>& rs) {
+            for (R* r : rs) {
+                r->out = 2 * r->in;
+                r->batch = (int)rs.size();
+            }
+            std::this_thread::sleep_for(std::chrono::milliseconds(1));
+        });
+        b.add_active(8);
+        std::atomic<int> bad{0}, shared{0};
+        std::vector<std::thread> th;
+        for (int t = 0; t < 8; t++)
+            th.emplace_back([&, t] {
+                for (int u = 0; u < 25; u++) {
+                    R r;
+                    r.in = 1000 * t + u;
+                    b.submit(&r);
+                    if (r.out != 2 * r.in) bad++;
+                    if (r.batch > 1) shared++;
+                }
+                b.add_active(-1);
+            });
+        for (auto& t : th) t.join();
+        auto st = b.stats();
+        check(bad.load() == 0, "batcher: each request gets its own result");
+        check(st.requests == 200, "batcher: every request ran once");
+        check(st.max_batch_seen <= 4, "batcher: batches capped at max_batch");
+        check(shared.load() > 0 && st.batches < 200, "batcher: concurrent requests share batches");
+    }
+    // 10. the window: a lone active caller runs at once; with another caller active
+    //     (but silent) the batch waits the window out
+    {
+        struct R {
+            int x = 0;
+        };
+        Batcher<R> b(std::chrono::milliseconds(60), 8, [](std::vector<R*>&) {});
+        b.add_active(1);
+        R r;
+        auto t0 = std::chrono::steady_clock::now();
+        b.submit(&r);
+        double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        check(dt < 0.04, "batcher: a lone caller does not wait for the window");
+        b.add_active(1);
+        t0 = std::chrono::steady_clock::now();
+        b.submit(&r);
+        dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        check(dt >= 0.05, "batcher: waits the window for the other active caller");
+        b.add_active(-2);
+    }
+    // 11. fini runs on the worker thread when the batcher is destroyed
+    {
+        std::atomic<bool> fini_ran{false};
+        std::thread::id worker_id, fini_id;
+        {
+            struct R {
+                int x = 0;
+            };
+            Batcher<R> b(
+                std::chrono::microseconds(100), 2,
+                [&](std::vector<R*>&) { worker_id = std::this_thread::get_id(); },
+                [&] {
+                    fini_id = std::this_thread::get_id();
+                    fini_ran = true;
+                });
+            R r;
+            b.submit(&r);
+        }
+        check(fini_ran.load() && fini_id == worker_id, "batcher: fini on the worker thread");
     }
     return g_fail;
 }
