@@ -418,7 +418,8 @@ def run_serving(args, rank, world, local):
     for _ in range(2):
         t0 = time.perf_counter()
         jid = srv.submit(ycal, [1.0] * 3, args.tol)
-        srv.wait(jid)
+        if not srv.wait(jid, 900.0):
+            raise RuntimeError("serving: the calibration job did not finish in 900 s")
         srv.result(jid)
         t_cal = time.perf_counter() - t0
     mean_n = float(np.mean(sides.astype(np.float64) ** 3))
@@ -437,7 +438,8 @@ def run_serving(args, rank, world, local):
         ids.append(srv.submit(boxes[j], [1.0] * 3, args.tol))
     results = []
     for jid in ids:
-        srv.wait(jid)
+        if not srv.wait(jid, 1800.0):
+            raise RuntimeError(f"serving: job {jid} did not finish in 1800 s")
         results.append(srv.result(jid))
     wall = time.perf_counter() - t_start
     launches = B.sdot_kernel_launches() - l0
