@@ -73,3 +73,43 @@ def test_bench_replicas_gloo_world2():
         assert p.exitcode == 0
     assert [o[1] for o in out] == [20.0, 20.0]  # both ranks see the max
     assert out[0][2] != out[1][2]                # independent boxes
+
+
+def test_header_is_plain_c_and_links(tmp_path):
+    # the C ABI is usable from C: the header compiles as C99 without warnings and a C
+    # program links the library and calls host-only entry points
+    import shutil
+    import subprocess
+
+    from paper_2110_08868_gb300 import build as b
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    lib = b.build()
+    src = tmp_path / "abi.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include "sdot.h"
+int main(void) {
+    sdot_options o;
+    sdot_server_options so;
+    double box[3] = {1.0, 1.0, 1.0};
+    size_t bytes = 0;
+    if (sdot_default_options(&o) != SDOT_OK || o.k != 24) return 1;
+    if (sdot_server_default_options(&so) != SDOT_OK || so.max_active != 8) return 2;
+    if (sdot_server_footprint(32768, box, &o, &bytes) != SDOT_OK || bytes == 0) return 3;
+    if (sdot_server_footprint(1, box, &o, &bytes) != SDOT_ERR_ARG) return 4;
+    printf("%zu %s\n", bytes, sdot_last_error());
+    return 0;
+}
+""")
+    exe = tmp_path / "abi"
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                        "-I", os.path.join(ROOT, "include"), str(src), lib,
+                        "-Wl,-rpath," + os.path.dirname(lib), "-o", str(exe)],
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    assert int(r.stdout.split()[0]) > 32768 * 1000
