@@ -2,8 +2,10 @@
 
 Every function keeps the C name and returns the C status code; the buffers may be
 numpy arrays (host memory) or torch tensors (host or CUDA memory). ``check``
-turns a status into an exception carrying ``sdot_last_error()``. The library must
-be built (``paper_2110_08868_gb300.build``); there is no fallback path.
+turns a status into an exception carrying ``sdot_last_error()``. ``Solver`` owns one
+context (one box), ``Server`` one reconstruction server (many boxes, queued and run
+concurrently). The library must be built (``paper_2110_08868_gb300.build``); there is
+no fallback path.
 """
 from __future__ import annotations
 
