@@ -347,6 +347,27 @@ def run_native(args, rank, world, local):
                                          "ms_cg", "ms_total", "ms_pass", "refined_fp64",
                                          "max_rel_err")},
              "roofline_pcg": spmv}
+    # one Laguerre evaluation at psi_a on a warm context (clip, re-queue, FP64 re-clip,
+    # reductions and the CSR Hessian; kNN and Newton excluded): cells/s per evaluation
+    try:
+        rc, ctx = B.sdot_create(pos_dev, None, box, opt)
+        B.check(rc)
+        try:
+            vol_dev = torch.empty(N, dtype=torch.float64, device="cuda")
+            hcsr = B.sdot_csr()
+            B.check(B.sdot_laguerre(ctx, psi_dev, vol_dev, None, hcsr))  # first diagram
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            B.check(B.sdot_laguerre(ctx, None, vol_dev, None, hcsr))  # warm: previous facets
+            torch.cuda.synchronize()
+            lag_ms = (time.perf_counter() - t0) * 1e3
+        finally:
+            B.sdot_destroy(ctx)
+        extra["laguerre_eval"] = {"ms": lag_ms, "cells_per_s": N / (lag_ms / 1e3),
+                                  "what": "one sdot_laguerre at psi_a with the CSR Hessian, "
+                                          "warm context, device buffers"}
+    except Exception as e:  # reported, never fatal to the bench line
+        extra["laguerre_eval"] = {"error": str(e)[:200]}
     if not args.no_fp64_compare and args.precision == "mixed":
         opt64 = B.sdot_default_options(precision="fp64")
         one_step(pos_dev, disp_dev, psi_dev, opt64)
