@@ -113,3 +113,40 @@ int main(void) {
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
     assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
     assert int(r.stdout.split()[0]) > 32768 * 1000
+
+
+def _bench(args, env_extra=None, timeout=600):
+    import json
+    import subprocess
+
+    env = dict(os.environ)
+    env.update(env_extra or {})
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + args,
+                       capture_output=True, text=True, timeout=timeout, env=env, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    return [json.loads(ln) for ln in lines]
+
+
+def test_bench_reference_arm_contract():
+    # the reference arm (the CPU oracle on a bounded sample) prints one JSON line with
+    # the keys of the bench contract; a small box keeps it fast
+    out = _bench(["--impl", "reference", "--steps", "1", "--warmup", "1",
+                  "--workload", "zeldovich-16^3-kinv-0.3a"])
+    assert len(out) == 1
+    line = out[0]
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+              "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 1
+    assert line["config"]["workload"] == "zeldovich-16^3-kinv-0.3a"
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+
+
+def test_bench_reference_arm_other_ranks_are_silent():
+    out = _bench(["--impl", "reference", "--steps", "1", "--warmup", "0",
+                  "--workload", "zeldovich-16^3-kinv-0.3a"],
+                 {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    assert out == []
