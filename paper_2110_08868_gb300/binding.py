@@ -284,6 +284,13 @@ class Solver:
             sdot_destroy(self.ctx)
             self.ctx = None
 
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
     def __del__(self):
         try:
             self.close()
@@ -470,6 +477,13 @@ class Server:
         if self.srv:
             sdot_server_destroy(self.srv)
             self.srv = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
 
     def __del__(self):
         try:

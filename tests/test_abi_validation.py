@@ -156,3 +156,8 @@ def test_allocator_needs_both_functions():
     assert B.sdot_set_allocator(alloc=lambda n: 0) == B.SDOT_ERR_ARG
     assert B.sdot_set_allocator(free=lambda p: None) == B.SDOT_ERR_ARG
     assert B.sdot_set_allocator() == B.SDOT_OK
+
+
+def test_wrappers_are_context_managers():
+    assert hasattr(B.Solver, "__enter__") and hasattr(B.Solver, "__exit__")
+    assert hasattr(B.Server, "__enter__") and hasattr(B.Server, "__exit__")
