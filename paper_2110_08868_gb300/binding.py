@@ -250,8 +250,27 @@ SDOT_STATIC_MAX_N = 32768
 SDOT_STATIC_MAX_K = 32
 
 
+def _check_knn_static_args(pos, k, nbr):
+    """Shapes and placement sdot_knn_static relies on: the C call cannot see buffer
+    sizes, so a (N, 2) pos or a short nbr would make its kernels read or write past
+    the caller's buffers. Raises ValueError."""
+    for name, t in (("pos", pos), ("nbr", nbr)):
+        if not hasattr(t, "is_cuda") or not t.is_cuda:
+            raise ValueError(f"sdot_knn_static: {name} must be a CUDA tensor")
+    if pos.dim() != 2 or pos.shape[1] != 3:
+        raise ValueError(f"sdot_knn_static: pos must have shape (N, 3), got {tuple(pos.shape)}")
+    n = int(pos.shape[0])
+    if tuple(nbr.shape) != (n, int(k)):
+        raise ValueError(f"sdot_knn_static: nbr must have shape ({n}, {int(k)}), "
+                         f"got {tuple(nbr.shape)}")
+    if pos.device != nbr.device:
+        raise ValueError("sdot_knn_static: pos and nbr must be on the same device")
+
+
 def sdot_knn_static(pos, box, k, nbr, stream=None):
-    """kNN lists without device allocation (pos, nbr: CUDA tensors; see include/sdot.h)."""
+    """kNN lists without device allocation (pos: (N, 3) float64, nbr: (N, k) int32, both
+    CUDA tensors on the current device; see include/sdot.h)."""
+    _check_knn_static_args(pos, k, nbr)
     b = np.ascontiguousarray(np.broadcast_to(np.asarray(box, dtype=np.float64), (3,)))
     h = getattr(stream, "cuda_stream", stream)
     return load().sdot_knn_static(_ptr(pos), int(pos.shape[0]), ctypes.c_void_p(b.ctypes.data),

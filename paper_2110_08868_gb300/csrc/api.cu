@@ -316,7 +316,7 @@ int create_context(const double* pos, const double* mass, int64_t N, const doubl
     // positions: device view (caller buffer or staging copy)
     const double* posd = nullptr;
     if ((rc = input_vec(c, pos, N * 3, c->stage, &posd))) return fail(rc);
-    if ((rc = build_grid(d, posd, c->opt.seeds_per_leaf, c->temp, s))) return fail(rc);
+    if ((rc = build_grid(d, posd, c->opt.seeds_per_leaf, c->temp, s, "sdot_create"))) return fail(rc);
     // masses in sorted order
     if (mass) {
         const double* md = nullptr;

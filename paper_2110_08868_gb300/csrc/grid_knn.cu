@@ -222,7 +222,7 @@ __global__ void finalize_sort_kernel(const double* __restrict__ pos_user, int64_
 }
 
 int build_grid(DeviceState& d, const double* pos_user_dev, double seeds_per_leaf, void* temp,
-               cudaStream_t s) {
+               cudaStream_t s, const char* who) {
     const int64_t N = d.N;
     double vol = d.L[0] * d.L[1] * d.L[2];
     double h = cbrt(seeds_per_leaf * vol / (double)N);
@@ -276,7 +276,7 @@ int build_grid(DeviceState& d, const double* pos_user_dev, double seeds_per_leaf
     SDOT_CUDA_TRY(cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, s));
     SDOT_CUDA_TRY(cudaStreamSynchronize(s));
     if (hbad) {
-        set_error("sdot_create: a position is not finite or lies outside [0, box)");
+        set_error(std::string(who) + ": a position is not finite or lies outside [0, box)");
         return SDOT_ERR_ARG;
     }
     return SDOT_OK;

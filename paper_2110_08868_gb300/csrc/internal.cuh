@@ -147,8 +147,9 @@ int scan_exclusive_i32(const int32_t* in, int32_t* out, int64_t n, void* temp,
                        cudaStream_t s);
 
 // grid_knn.cu
+// who: the public entry point, named in the error message
 int build_grid(DeviceState& d, const double* pos_user_dev, double seeds_per_leaf,
-               void* temp, cudaStream_t s);
+               void* temp, cudaStream_t s, const char* who);
 int build_knn(DeviceState& d, cudaStream_t s, int* dup_flag_host);
 int knn_to_user(const DeviceState& d, int32_t* out_user_dev, cudaStream_t s);
 

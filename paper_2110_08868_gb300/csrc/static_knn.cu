@@ -92,12 +92,22 @@ extern "C" int sdot_knn_static(const double* pos, int64_t N, const double box[3]
             set_error("sdot_knn_static: box lengths must be finite and positive");
             return SDOT_ERR_ARG;
         }
+    int cur_dev = 0;
+    SDOT_CUDA_TRY(cudaGetDevice(&cur_dev));
     for (const void* p : {(const void*)pos, (const void*)nbr}) {
         cudaPointerAttributes at;
         if (cudaPointerGetAttributes(&at, p) != cudaSuccess ||
             (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
             cudaGetLastError();
             set_error("sdot_knn_static: pos and nbr must be device (or managed) memory");
+            return SDOT_ERR_ARG;
+        }
+        // the kernels run on the current device against that device's scratch array;
+        // memory of another device would be reached through peer access, if at all
+        if (at.type == cudaMemoryTypeDevice && at.device != cur_dev) {
+            set_error("sdot_knn_static: pos and nbr must live on the current device (device " +
+                      std::to_string(cur_dev) + "), one of them is on device " +
+                      std::to_string(at.device));
             return SDOT_ERR_ARG;
         }
     }
@@ -131,7 +141,7 @@ extern "C" int sdot_knn_static(const double* pos, int64_t N, const double box[3]
         set_error("sdot_knn_static: box aspect gives more grid cells than seeds");
         return SDOT_ERR_ARG;
     }
-    if ((rc = build_grid(d, pos, 2.0, base + ST_TEMP, s))) return rc;
+    if ((rc = build_grid(d, pos, 2.0, base + ST_TEMP, s, "sdot_knn_static"))) return rc;
     int kflags = 0;
     if ((rc = build_knn(d, s, &kflags))) return rc;
     if (kflags & 1) {

@@ -161,3 +161,36 @@ def test_allocator_needs_both_functions():
 def test_wrappers_are_context_managers():
     assert hasattr(B.Solver, "__enter__") and hasattr(B.Solver, "__exit__")
     assert hasattr(B.Server, "__enter__") and hasattr(B.Server, "__exit__")
+
+
+class _FakeCudaTensor:
+    """Just enough of a CUDA tensor for the binding's shape checks (no device needed)."""
+
+    def __init__(self, shape, device="cuda:0"):
+        self.shape = tuple(shape)
+        self.is_cuda = True
+        self.device = device
+
+    def dim(self):
+        return len(self.shape)
+
+
+@pytest.mark.parametrize("pos_shape,nbr_shape,k,devs,msg", [
+    ((100, 2), (100, 8), 8, ("cuda:0", "cuda:0"), "pos must have shape (N, 3)"),
+    ((100, 3, 1), (100, 8), 8, ("cuda:0", "cuda:0"), "pos must have shape (N, 3)"),
+    ((100, 3), (100, 7), 8, ("cuda:0", "cuda:0"), "nbr must have shape (100, 8)"),
+    ((100, 3), (99, 8), 8, ("cuda:0", "cuda:0"), "nbr must have shape (100, 8)"),
+    ((100, 3), (100 * 8,), 8, ("cuda:0", "cuda:0"), "nbr must have shape (100, 8)"),
+    ((100, 3), (100, 8), 8, ("cuda:0", "cuda:1"), "same device"),
+])
+def test_knn_static_wrapper_rejects_bad_buffers(pos_shape, nbr_shape, k, devs, msg):
+    # the C call cannot see buffer sizes, so the binding refuses them before calling it
+    pos = _FakeCudaTensor(pos_shape, devs[0])
+    nbr = _FakeCudaTensor(nbr_shape, devs[1])
+    with pytest.raises(ValueError, match=msg.replace("(", r"\(").replace(")", r"\)")):
+        B.sdot_knn_static(pos, [1.0] * 3, k, nbr)
+
+
+def test_knn_static_wrapper_rejects_host_buffers():
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        B.sdot_knn_static(_pos(100), [1.0] * 3, 8, np.zeros((100, 8), np.int32))

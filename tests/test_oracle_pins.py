@@ -155,6 +155,52 @@ def test_brute_equals_certified():
         np.testing.assert_allclose(Lb, Lc, atol=1e-12 * np.abs(Lb).max())
 
 
+def test_brute_equals_certified_at_solved_clumpy_psi():
+    # psi of an oracle-solved clumpy box spreads over ~5 a^2 (the regime of the
+    # 256^3 + clumps workload, whose solved psi spreads over several a^2), so the
+    # certificate's psi term R + sqrt(R^2 + 2 (psi_max - psi_i)) decides where the
+    # certified cells stop
+    n, L = 7, 1.0
+    a = L / n
+    y, _, _ = ics.zeldovich_box(n, L, ics.spectrum_kinv, 0.3, 5)
+    y = np.ascontiguousarray(ics.add_clumps(y, L, n, 1, 120, 0.05, 6))
+    N = y.shape[0]
+    psi, info = O.solve(y, ics.uniform_masses(N, L), L, tol=1e-10)
+    assert (psi.max() - psi.min()) > 4.0 * a * a
+    b = O.cells(y, psi, L, "brute")
+    c = O.cells(y, psi, L, "certified")
+    np.testing.assert_allclose(b["vol"], c["vol"], rtol=1e-12, atol=0)
+    np.testing.assert_allclose(b["m1"], c["m1"], atol=1e-14 * a ** 4)
+    Lb = O.hessian_laplacian(b, N).toarray()
+    Lc = O.hessian_laplacian(c, N).toarray()
+    np.testing.assert_allclose(Lb, Lc, atol=1e-12 * np.abs(Lb).max())
+
+
+@pytest.mark.parametrize("n,dist,dpsi", [(5, 2, 1.5), (7, 3, 3.75)])
+@pytest.mark.parametrize("mode", ["brute", "certified"])
+def test_hidden_heavy_neighbour_closed_form(n, dist, dpsi, mode):
+    # Lattice, psi = 0 except psi_j = dpsi a^2 for the seed j that sits `dist` spacings
+    # along +x from seed i. Its bisector with i, p_x <= (dist^2 a^2 / 2 - dpsi a^2) /
+    # (dist a) = a/4, cuts the cube cell of i although j is no face neighbour, and j's
+    # image on the other side (n - dist spacings away) does not reach it. So
+    # V_i = 3/4 a^3 and the local centroid is (-a/8, 0, 0). A certificate without the
+    # psi term (2R = sqrt(3) a) stops before j in both cases; one with half the psi term
+    # (R + sqrt(R^2 + dpsi)) stops before j in the (7, 3) case.
+    L = 1.0
+    a = L / n
+    y = ics.lattice(n, L)
+    N = n ** 3
+    i = (n // 2) * (1 + n + n * n) - dist // 2  # an interior seed; j = i + dist along x
+    j = i + dist
+    assert np.isclose(y[j, 0] - y[i, 0], dist * a)
+    psi = np.zeros(N)
+    psi[j] = dpsi * a * a
+    c = O.cells(y, psi, L, mode, idx=np.array([i]))
+    np.testing.assert_allclose(c["vol"][0], 0.75 * a ** 3, rtol=1e-12)
+    np.testing.assert_allclose(c["m1"][0] / c["vol"][0], [-a / 8, 0.0, 0.0], atol=1e-13 * a)
+    assert j in set(c["fj"][0, :c["nfac"][0]].tolist())
+
+
 def test_invariants():
     y, psi, L = _random_case(n=6, seed=11)
     N = y.shape[0]
