@@ -42,7 +42,7 @@ def _stale(out, deps):
 def build(verbose=False, force=False, extra=()):
     os.makedirs(BUILD, exist_ok=True)
     hdrs = [os.path.join(CSRC, "internal.cuh"), os.path.join(CSRC, "serve_sched.h"),
-            os.path.join(INCLUDE, "sdot.h")]
+            os.path.join(CSRC, "cell.cuh"), os.path.join(INCLUDE, "sdot.h")]
     objs = []
     jobs = []
     for src in SOURCES:

@@ -208,6 +208,7 @@ int alloc_context(sdot_ctx* c) {
         (rc = alloc_n(c, &d.m1, N * 3)) || (rc = alloc_n(c, &d.anchor, N * 3)) ||
         (rc = alloc_n(c, &d.status, N)) || (rc = alloc_n(c, &d.fcnt, N)) ||
         (rc = alloc_n(c, &d.fcol, N * FCAP)) || (rc = alloc_n(c, &d.fval, N * FCAP)) ||
+        (rc = alloc_n(c, &d.topo, N * TOPO)) || (rc = alloc_n(c, &d.topo_n, N)) ||
         (rc = alloc_n(c, &d.queue, N)) || (rc = alloc_n(c, &d.queue64, N)) ||
         (rc = alloc_n(c, &d.counters, 32)) || (rc = alloc_n(c, &d.row_ptr, N + 1)) ||
         (rc = alloc_n(c, &d.rowcnt, N + 1)) || (rc = alloc_n(c, &d.x, N)) ||
@@ -359,6 +360,7 @@ int create_context(const double* pos, const double* mass, int64_t N, const doubl
         cudaMemsetAsync(d.fcnt, 0, (size_t)N * 4, s) != cudaSuccess ||
         cudaMemsetAsync(d.fcol, 0, (size_t)N * FCAP * 4, s) != cudaSuccess ||
         cudaMemsetAsync(d.fval, 0, (size_t)N * FCAP * 8, s) != cudaSuccess ||
+        cudaMemsetAsync(d.topo_n, 0, (size_t)N, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
         set_error("sdot_create: initialisation failed");
         return fail(SDOT_ERR_CUDA);

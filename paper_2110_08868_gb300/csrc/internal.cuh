@@ -28,13 +28,11 @@ struct __align__(32) Pos4 {
 // capacities
 // ---------------------------------------------------------------------------
 constexpr int KMAX = 64;        // largest kNN size
-constexpr int MAXP = 96;        // planes per polytope (6 box planes included)
-constexpr int MAXT = 192;       // vertices (dual triangles) per polytope
+constexpr int MAXP = 96;        // planes of the largest polytope (6 box planes included)
+constexpr int MAXT = 192;       // vertices (dual triangles) of the largest polytope
 constexpr int FCAP = 64;        // facets stored per cell for the Hessian
-constexpr int MAXFV = 32;       // vertices per face during integration
-constexpr int STACK = 256;      // traversal stack entries per warp
+constexpr int TOPO = 64;        // vertices of a cell's stored topology (warm start)
 constexpr int MAXLEV = 8;       // pyramid levels
-constexpr int WARPS_PER_BLOCK = 4;
 
 // cell status bits (per cell, uint8)
 enum : uint32_t {
@@ -94,6 +92,9 @@ struct DeviceState {
     int32_t* fcnt;            // N facet counts
     int32_t* fcol;            // N * FCAP facet neighbours (sorted index)
     double* fval;             // N * FCAP facet coefficients A/|d|
+    uint32_t* topo;           // N * TOPO vertices of each cell as three plane indices
+                              // (0..5 box faces, 6 + k facet k of fcol)
+    uint8_t* topo_n;          // N vertex counts of topo (0: none stored)
     int32_t* queue;           // N, re-queued cells
     int32_t* queue64;         // N, cells for the FP64 re-clip
     int32_t* counters;        // [0] requeue count [1] fp64 count [2] work counter
