@@ -44,6 +44,7 @@ struct sdot_ctx {
     int64_t nnz_cap = 0;
     int64_t nnz = 0;
     int64_t nnz_cap_u = 0;
+    int64_t sell_cap = 0;     // entries the sliced-ELL arrays hold
     bool eval_valid = false;  // last evaluation is at d.psi
     float ms_knn = 0;
     EvalResult last{};
@@ -180,6 +181,25 @@ int build_csr(sdot_ctx* c) {
     return SDOT_OK;
 }
 
+// the sliced-ELL Newton matrix: count, grow the arrays if needed (8 bytes of value per
+// entry, enough for either precision), fill
+int build_sell(sdot_ctx* c, int mixed) {
+    int64_t ent = 0;
+    int rc = sell_build(c->d, &ent, mixed, c->stream);
+    if (rc) return rc;
+    if (ent > c->sell_cap) {
+        dev_free(c, c->d.sell_col);
+        dev_free(c, c->d.sell_val);
+        c->d.sell_col = nullptr;
+        c->d.sell_val = nullptr;
+        const int64_t cap = ent + ent / 4 + 1024;
+        if ((rc = alloc_n(c, &c->d.sell_col, cap))) return rc;
+        if ((rc = dev_alloc(c, &c->d.sell_val, (size_t)cap * 8))) return rc;
+        c->sell_cap = cap;
+    }
+    return sell_fill(c->d, mixed, c->stream);
+}
+
 // Every device array of a context for d.N seeds in box d.L (the hash grid, kNN lists,
 // facet slab, PCG vectors, psi pyramid, temp). With c->dry set nothing is allocated
 // and c->bytes receives the total, which is the footprint of a server job.
@@ -213,7 +233,9 @@ int alloc_context(sdot_ctx* c) {
         (rc = alloc_n(c, &d.counters, 32)) || (rc = alloc_n(c, &d.row_ptr, N + 1)) ||
         (rc = alloc_n(c, &d.rowcnt, N + 1)) || (rc = alloc_n(c, &d.x, N)) ||
         (rc = alloc_n(c, &d.r, N)) || (rc = alloc_n(c, &d.z, N)) || (rc = alloc_n(c, &d.p, N)) ||
-        (rc = alloc_n(c, &d.q, N)) || (rc = alloc_n(c, &d.dinv, N)) ||
+        (rc = alloc_n(c, &d.q, N)) || (rc = alloc_n(c, &d.sv, N)) ||
+        (rc = alloc_n(c, &d.dinv, N)) || (rc = alloc_n(c, &d.sell_ptr, (N + 31) / 32 + 1)) ||
+        (rc = alloc_n(c, &d.sell_w, (N + 31) / 32 + 1)) ||
         (rc = alloc_n(c, &d.partials, 1 << 20)) || (rc = alloc_n(c, &d.scal, 64)) ||
         (rc = alloc_n(c, &d.grid.cell_start, ncell + 1)) || (rc = alloc_n(c, &c->stage, N * 3)))
         return rc;
@@ -402,8 +424,9 @@ int context_footprint(int64_t N, const double box[3], const sdot_options* opt, s
     d.a = cbrt(box[0] * box[1] * box[2] / (double)N);
     int rc = alloc_context(&c);
     if (rc) return rc;
-    // CSR: 25 entries per seed (int32 column + FP64 value), the capacity sdot_solve
-    // grows to on Zel'dovich boxes (about 17 nonzeros per row, 25% headroom)
+    // Newton matrix: 25 entries per seed (int32 column + 8-byte value), the sliced-ELL
+    // capacity sdot_solve grows to on Zel'dovich boxes (about 17 entries per row padded
+    // to the longest row of each slice of 32, 25% headroom)
     *bytes = c.bytes + ((size_t)N * 25 * 12 + 511) / 512 * 512;
     return SDOT_OK;
 }
@@ -605,11 +628,11 @@ int sdot_solve(sdot_ctx* c, double tol, const double* psi0, sdot_stats* st) {
             rc = SDOT_ERR_MAXIT;
             break;
         }
-        if ((rc = build_csr(c))) break;
+        if ((rc = build_sell(c, c->opt.precision == SDOT_PREC_MIXED))) break;
         int cg_it = 0;
         double cg_res = 0;
         cudaEventRecord(c0, s);
-        if ((rc = pcg_solve(d, c->opt.cg_rtol, c->opt.cg_maxit, &cg_it, &cg_res, s))) break;
+        if ((rc = cg_solve(d, c->opt.cg_rtol, c->opt.cg_maxit, &cg_it, &cg_res, s))) break;
         cudaEventRecord(c1, s);
         cudaEventSynchronize(c1);
         float ms = 0;

@@ -176,6 +176,11 @@ __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULLMASK, v, o);
     return v;
 }
+template <typename R>
+__device__ __forceinline__ R warp_sum_r(R v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULLMASK, v, o);
+    return v;
+}
 
 template <typename R, class C>
 __device__ __forceinline__ V3<R> vert(const Poly<R, C>& P, int s) {
@@ -932,7 +937,15 @@ __device__ __noinline__ int process_leaves(Poly<R, C>& P, const ClipParams& cp,
         uint32_t cm = __ballot_sync(FULLMASK, cand);
         WCOUNT(P, 5, __popc(cm));
         if (!cm) continue;
-        // exact planes of the candidates, one per lane
+        // drop the seeds that already are planes of the polytope (the cell's own facet
+        // neighbours pass the prefilter), then build the exact planes of the rest
+        for (uint32_t m2 = cm; m2;) {
+            const int src = __ffs(m2) - 1;
+            m2 &= m2 - 1;
+            if (has_plane(P, __shfl_sync(FULLMASK, s, src), lane)) cm &= ~(1u << src);
+        }
+        if (!cm) continue;
+        cand = (cm >> lane) & 1u;
         V4<R> pl;
         pl.x = pl.y = pl.z = pl.w = R(0);
         R len = R(1);
@@ -943,7 +956,9 @@ __device__ __noinline__ int process_leaves(Poly<R, C>& P, const ClipParams& cp,
             const int32_t j = __shfl_sync(FULLMASK, s, src);
             const V4<R> pn = shfl_plane(pl, src);
             const R plen = __shfl_sync(FULLMASK, len, src);
-            if (has_plane(P, j, lane)) continue;  // already one of the planes
+            // an earlier clip of this round may have added the same seed? (seeds are
+            // distinct within a round, so only FULL mode's clips can change the set)
+            if (MODE == MODE_FULL && has_plane(P, j, lane)) continue;
             if (MODE == MODE_CERTIFY) {
                 if (poly_cut_by(P, pn, plen, lane)) {
                     st |= CS_UNCERTIFIED;
@@ -1068,7 +1083,10 @@ template <typename R, class C>
 __device__ __noinline__ bool integrate(Poly<R, C>& P, const ClipParams& cp, const Frame& fr,
                                        int64_t i, int lane, bool& bad, uint32_t& st,
                                        float* cen) {
-    double vol6 = 0, mx = 0, my = 0, mz = 0, sx = 0, sy = 0, sz = 0, sabs = 0;
+    // volume and first moment: summed per face in R, the face totals in FP64; the
+    // surface closure check and the facet areas in R
+    double vol6 = 0, mx = 0, my = 0, mz = 0;
+    R sx = 0, sy = 0, sz = 0, sabs = 0;
     constexpr int FPL = (C::MP + 31) / 32;  // faces handled per lane
     // apex of the tetrahedron fans: the centre o of the vertices' bounding box, so the
     // determinants involve offsets of the cell's own size even when the cell lies far
@@ -1163,6 +1181,7 @@ __device__ __noinline__ bool integrate(Poly<R, C>& P, const ClipParams& cp, cons
         v0.z -= o[2];
         V3<R> vp = v0;
         R Sx = 0, Sy = 0, Sz = 0;
+        R fv6 = 0, fmx = 0, fmy = 0, fmz = 0;
         bool ok = true;
         for (int step = 1; step < m; step++) {
             const uint32_t yv = (ecur >> 8) & 0xff;
@@ -1190,11 +1209,11 @@ __device__ __noinline__ bool integrate(Poly<R, C>& P, const ClipParams& cp, cons
                 Sy += cy;
                 Sz += cz;
                 // 6 |tet(o, v0, vp, vc)| = det(v0, vp, vc) with vertices relative to o
-                const double d6 = (double)(v0.x * cx + v0.y * cy + v0.z * cz);
-                vol6 += d6;
-                mx += d6 * ((double)v0.x + (double)vp.x + (double)vc.x);
-                my += d6 * ((double)v0.y + (double)vp.y + (double)vc.y);
-                mz += d6 * ((double)v0.z + (double)vp.z + (double)vc.z);
+                const R d6 = v0.x * cx + v0.y * cy + v0.z * cz;
+                fv6 += d6;
+                fmx += d6 * (v0.x + vp.x + vc.x);
+                fmy += d6 * (v0.y + vp.y + vc.y);
+                fmz += d6 * (v0.z + vp.z + vc.z);
             }
             vp = vc;
         }
@@ -1203,17 +1222,21 @@ __device__ __noinline__ bool integrate(Poly<R, C>& P, const ClipParams& cp, cons
             bad = true;
             continue;
         }
-        const double ax2 = 0.5 * (double)Sx, ay2 = 0.5 * (double)Sy, az2 = 0.5 * (double)Sz;
-        const double A = sqrt(ax2 * ax2 + ay2 * ay2 + az2 * az2);
+        vol6 += (double)fv6;
+        mx += (double)fmx;
+        my += (double)fmy;
+        mz += (double)fmz;
+        const R ax2 = R(0.5) * Sx, ay2 = R(0.5) * Sy, az2 = R(0.5) * Sz;
+        const R A = sqrt(ax2 * ax2 + ay2 * ay2 + az2 * az2);
         sx += ax2;
         sy += ay2;
         sz += az2;
         sabs += A;
         const int32_t j = P.pj[f];
-        if (j >= 0 && A > 0.0) {
+        if (j >= 0 && A > R(0)) {
             if (nf < FPL) {
                 fj[nf] = j;
-                fc[nf] = A * cp.a / (double)P.plen[f];
+                fc[nf] = (double)(A / P.plen[f]) * cp.a;
                 fslot[nf] = f;
             }
             nf++;
@@ -1223,10 +1246,10 @@ __device__ __noinline__ bool integrate(Poly<R, C>& P, const ClipParams& cp, cons
     mx = warp_sum(mx);
     my = warp_sum(my);
     mz = warp_sum(mz);
-    sx = warp_sum(sx);
-    sy = warp_sum(sy);
-    sz = warp_sum(sz);
-    sabs = warp_sum(sabs);
+    sx = warp_sum_r(sx);
+    sy = warp_sum_r(sy);
+    sz = warp_sum_r(sz);
+    sabs = warp_sum_r(sabs);
     // facets
     int incl = nf;
     for (int q = 1; q < 32; q <<= 1) {
@@ -1260,8 +1283,8 @@ __device__ __noinline__ bool integrate(Poly<R, C>& P, const ClipParams& cp, cons
         else cp.topo[i * TOPO + s2] = pack3(a, b2, c);
     }
     tok = __all_sync(FULLMASK, tok);
-    const double closure = sqrt(sx * sx + sy * sy + sz * sz);
-    const double tol = sizeof(R) == 4 ? 1e-4 : 1e-10;
+    const R closure = sqrt(sx * sx + sy * sy + sz * sz);
+    const R tol = sizeof(R) == 4 ? R(1e-4) : R(1e-10);
     if (!(closure <= tol * sabs)) bad = true;
     const double vol = vol6 / 6.0;
     if (!(vol > 0.0) || !isfinite(vol)) bad = true;

@@ -109,8 +109,16 @@ struct DeviceState {
     int64_t* row_ptr_u;
     int32_t* col_u;
     double* val_u;
-    // PCG vectors
-    double *x, *r, *z, *p, *q, *dinv;
+    // CG vectors (x: the Newton direction, z: u = M^-1 r, q: w = L u, sv: s = L p)
+    double *x, *r, *z, *p, *q, *sv, *dinv;
+    // the Newton matrix L in sliced-ELL form (slices of 32 rows, entry k of row
+    // 32 l + m at sell_ptr[l] + 32 k + m): neighbour column and weight A/|d| (FP32 in
+    // mixed precision, else FP64); the diagonal is implied (zero row sums)
+    int64_t* sell_ptr;        // nslice + 1
+    int32_t* sell_w;          // nslice + 1 slice widths (scan input)
+    int32_t* sell_col;
+    void* sell_val;
+    int sell_mixed;
     double* partials;         // reduction partials
     double* scal;             // device scalars
     Grid grid;
@@ -182,8 +190,13 @@ typedef int (*EvalHook)(void* user, DeviceState* d, const double* psi, int preci
 int csr_count(DeviceState& d, int64_t* nnz_out, cudaStream_t s);  // row_ptr and nnz
 int csr_fill(DeviceState& d, cudaStream_t s);                      // col, val, dinv
 int assemble_csr_user(DeviceState& d, int64_t nnz, cudaStream_t s);
-int pcg_solve(DeviceState& d, double rtol, int maxit, int* iters, double* rel_res,
-              cudaStream_t s);
+// sliced-ELL Newton matrix: sell_build counts (sell_ptr in slice widths, *entries the
+// storage it needs), sell_fill writes it (arrays of that capacity) and dinv
+int sell_build(DeviceState& d, int64_t* entries, int mixed, cudaStream_t s);
+int sell_fill(DeviceState& d, int mixed, cudaStream_t s);
+// Jacobi-preconditioned CG on L x = (nu - V) - mean, until ||r|| <= rtol ||r0||
+int cg_solve(DeviceState& d, double rtol, int maxit, int* iters, double* rel_res,
+             cudaStream_t s);
 int axpy_gauge(DeviceState& d, const double* psi, const double* delta, double alpha,
                double* out, cudaStream_t s);
 int subtract_mean(DeviceState& d, double* v, cudaStream_t s);

@@ -168,13 +168,13 @@ int assemble_csr_user(DeviceState& d, int64_t nnz, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// PCG
+// Newton system: sliced-ELL matrix and conjugate gradients
 // ---------------------------------------------------------------------------
-constexpr int PCG_THREADS = 256;
+constexpr int CG_THREADS = 256;
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULLMASK, v, o);
-    int w = threadIdx.x >> 5;
+    const int w = threadIdx.x >> 5;
     __syncthreads();
     if ((threadIdx.x & 31) == 0) sh[w] = v;
     __syncthreads();
@@ -184,150 +184,298 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return t;  // valid in thread 0
 }
 
-// fixed-order sum of nb partials with stride; every block gets the same value
-__device__ __forceinline__ double sum_partials(const double* __restrict__ part, int nb, int stride,
-                                               double* sh) {
-    double v = 0;
-    // each thread sums a fixed subset, then a fixed-order block reduction
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += part[(int64_t)b * stride];
-    double t = block_sum(v, sh);
-    __shared__ double bc;
-    if (threadIdx.x == 0) bc = t;
-    __syncthreads();
-    return bc;
+// Off-diagonal entries kept per row (symmetrised facets of positive weight); one warp
+// per slice of 32 rows, whose width (longest row) it records.
+__global__ void sell_count_kernel(const int32_t* __restrict__ fcnt, const int32_t* __restrict__ fcol,
+                                  const double* __restrict__ fval, int64_t N, int64_t nslice,
+                                  int32_t* __restrict__ width) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t sl = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); sl < nslice;
+         sl += nw) {
+        const int64_t i = sl * 32 + lane;
+        int kept = 0;
+        if (i < N) {
+            const int n = fcnt[i];
+            for (int t = 0; t < n; t++)
+                if (sym_value(fcnt, fcol, fval, i, t) > 0.0) kept++;
+        }
+        const int w = __reduce_max_sync(FULLMASK, kept);
+        if (lane == 0) width[sl] = w;
+    }
 }
 
-// r = g - mean, x = 0, z = dinv r, p = z; partials (r.z, r.r) into partB
-__global__ void pcg_init_kernel(const double* __restrict__ nu, const double* __restrict__ vol,
-                                double mean, const double* __restrict__ dinv, int64_t N,
-                                double* __restrict__ x, double* __restrict__ r,
-                                double* __restrict__ z, double* __restrict__ p,
-                                double* __restrict__ partB) {
+// The entries of each slice column by column (entry k of row 32 sl + l at
+// ptr[sl] + 32 k + l), padded with zero weights on the row's own column; the
+// Jacobi inverse diagonal from the stored (rounded) weights, so the stored matrix has
+// exactly zero row sums.
+template <typename T>
+__global__ void sell_fill_kernel(const int32_t* __restrict__ fcnt, const int32_t* __restrict__ fcol,
+                                 const double* __restrict__ fval, int64_t N, int64_t nslice,
+                                 const int64_t* __restrict__ ptr, int32_t* __restrict__ col,
+                                 T* __restrict__ val, double* __restrict__ dinv) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t sl = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); sl < nslice;
+         sl += nw) {
+        const int64_t i = sl * 32 + lane;
+        const int64_t base = ptr[sl] + lane;
+        const int w = (int)((ptr[sl + 1] - ptr[sl]) >> 5);
+        int k = 0;
+        double diag = 0.0;
+        if (i < N) {
+            const int n = fcnt[i];
+            for (int t = 0; t < n && k < w; t++) {
+                const double v = sym_value(fcnt, fcol, fval, i, t);
+                if (!(v > 0.0)) continue;
+                const T vt = (T)v;
+                col[base + 32 * (int64_t)k] = fcol[i * FCAP + t];
+                val[base + 32 * (int64_t)k] = vt;
+                diag += (double)vt;
+                k++;
+            }
+            dinv[i] = diag > 0.0 ? 1.0 / diag : 0.0;
+        }
+        const int32_t self = i < N ? (int32_t)i : 0;
+        for (; k < w; k++) {
+            col[base + 32 * (int64_t)k] = self;
+            val[base + 32 * (int64_t)k] = (T)0;
+        }
+    }
+}
+
+// Chronopoulos-Gear form of Jacobi-preconditioned CG (one reduction point per
+// iteration): with u = M^-1 r, w = L u, gamma = (r, u), delta = (w, u),
+//   beta = gamma / gamma_old, alpha = gamma / (delta - beta gamma / alpha_old)
+//   (first iteration: beta = 0, alpha = gamma / delta),
+//   p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s.
+// The SpMV kernel computes w and the partials of delta; its last block to finish
+// (counter + fence, no waiting) sums the partials of delta and of the gamma and (r, r)
+// left by the update kernel, in block order, and writes the scalars. Scalars in
+// cg[]: 0 alpha, 1 beta, 2 gamma_old, 3 alpha_old, 4 (r, r), 5 first-iteration flag.
+__global__ void cg_init_kernel(const double* __restrict__ nu, const double* __restrict__ vol,
+                               double mean, const double* __restrict__ dinv, int64_t N,
+                               double* __restrict__ x, double* __restrict__ r,
+                               double* __restrict__ u, double* __restrict__ p,
+                               double* __restrict__ sv, double* __restrict__ part,
+                               double* __restrict__ cg) {
     __shared__ double sh[32];
-    double rz = 0, rr = 0;
+    double g = 0, rr = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
-        double ri = (nu[i] - vol[i]) - mean;
-        double zi = dinv[i] * ri;
+        const double ri = (nu[i] - vol[i]) - mean;
+        const double ui = dinv[i] * ri;
         x[i] = 0.0;
         r[i] = ri;
-        z[i] = zi;
-        p[i] = zi;
-        rz += ri * zi;
+        u[i] = ui;
+        p[i] = 0.0;
+        sv[i] = 0.0;
+        g += ri * ui;
         rr += ri * ri;
     }
-    double a = block_sum(rz, sh);
-    double b = block_sum(rr, sh);
+    const double a = block_sum(g, sh);
+    const double b = block_sum(rr, sh);
     if (threadIdx.x == 0) {
-        partB[blockIdx.x * 2] = a;
-        partB[blockIdx.x * 2 + 1] = b;
+        part[3 * blockIdx.x + 0] = a;
+        part[3 * blockIdx.x + 2] = b;
+        if (blockIdx.x == 0) cg[5] = 1.0;
     }
 }
 
-// q = L p (8 lanes per row), partials of p.q into partA
-__global__ void pcg_spmv_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                                const double* __restrict__ val, const double* __restrict__ p,
-                                int64_t N, double* __restrict__ q, double* __restrict__ partA) {
+template <typename T>
+__global__ void __launch_bounds__(CG_THREADS)
+    cg_spmv_kernel(const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                   const T* __restrict__ val, int64_t N, int64_t nslice,
+                   const double* __restrict__ u, double* __restrict__ w,
+                   double* __restrict__ part, unsigned int* __restrict__ done,
+                   double* __restrict__ cg) {
     __shared__ double sh[32];
-    const int sub = threadIdx.x & 7;
-    double pq = 0;
-    const int64_t groups = (int64_t)gridDim.x * (blockDim.x >> 3);
-    const int64_t g0 = (int64_t)blockIdx.x * (blockDim.x >> 3) + (threadIdx.x >> 3);
-    const int64_t niter = (N + groups - 1) / groups;  // same for every lane
-    for (int64_t it = 0; it < niter; it++) {
-        const int64_t i = g0 + it * groups;
-        double acc = 0;
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    double dl = 0.0;
+    for (int64_t sl = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); sl < nslice;
+         sl += nw) {
+        const int64_t i = sl * 32 + lane;
+        const int64_t b0 = ptr[sl];
+        const int wd = (int)((ptr[sl + 1] - b0) >> 5);
+        const double ui = i < N ? u[i] : 0.0;
+        double acc = 0.0;
+        const int32_t* cp = col + b0 + lane;
+        const T* vp = val + b0 + lane;
+        int k = 0;
+        for (; k + 4 <= wd; k += 4) {
+            const int32_t j0 = cp[0], j1 = cp[32], j2 = cp[64], j3 = cp[96];
+            const T c0 = vp[0], c1 = vp[32], c2 = vp[64], c3 = vp[96];
+            const double u0 = u[j0], u1 = u[j1], u2 = u[j2], u3 = u[j3];
+            acc += (double)c0 * (ui - u0);
+            acc += (double)c1 * (ui - u1);
+            acc += (double)c2 * (ui - u2);
+            acc += (double)c3 * (ui - u3);
+            cp += 128;
+            vp += 128;
+        }
+        for (; k < wd; k++) {
+            acc += (double)vp[0] * (ui - u[cp[0]]);
+            cp += 32;
+            vp += 32;
+        }
         if (i < N) {
-            int64_t b = row_ptr[i], e = row_ptr[i + 1];
-            for (int64_t t = b + sub; t < e; t += 8) acc += val[t] * p[col[t]];
-        }
-        acc += __shfl_xor_sync(FULLMASK, acc, 4);
-        acc += __shfl_xor_sync(FULLMASK, acc, 2);
-        acc += __shfl_xor_sync(FULLMASK, acc, 1);
-        if (sub == 0 && i < N) {
-            q[i] = acc;
-            pq += acc * p[i];
+            w[i] = acc;
+            dl += acc * ui;
         }
     }
-    double a = block_sum(pq, sh);
-    if (threadIdx.x == 0) partA[blockIdx.x] = a;
+    const double a = block_sum(dl, sh);
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x + 1] = a;
+        __threadfence();
+        last = atomicAdd(done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    // the last block: fixed-order sums of the partials, then the scalars
+    __threadfence();
+    double sg = 0, sd = 0, sr = 0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+        sg += __ldcg(&part[3 * b + 0]);
+        sd += __ldcg(&part[3 * b + 1]);
+        sr += __ldcg(&part[3 * b + 2]);
+    }
+    const double G = block_sum(sg, sh);
+    const double D = block_sum(sd, sh);
+    const double RR = block_sum(sr, sh);
+    if (threadIdx.x == 0) {
+        double alpha, beta;
+        if (cg[5] != 0.0) {
+            beta = 0.0;
+            alpha = D != 0.0 ? G / D : 0.0;
+        } else {
+            beta = cg[2] != 0.0 ? G / cg[2] : 0.0;
+            const double den = D - beta * G / cg[3];
+            alpha = den != 0.0 ? G / den : 0.0;
+        }
+        cg[0] = alpha;
+        cg[1] = beta;
+        cg[2] = G;
+        cg[3] = alpha;
+        cg[4] = RR;
+        cg[5] = 0.0;
+        *done = 0u;
+    }
 }
 
-__global__ void pcg_update_kernel(const double* __restrict__ partA, const double* __restrict__ partB_prev,
-                                  double* __restrict__ partB_cur, int nb,
-                                  const double* __restrict__ dinv, int64_t N,
-                                  double* __restrict__ x, double* __restrict__ r,
-                                  double* __restrict__ z, const double* __restrict__ p,
-                                  const double* __restrict__ q) {
+__global__ void cg_update_kernel(const double* __restrict__ cg, const double* __restrict__ dinv,
+                                 int64_t N, const double* __restrict__ w, double* __restrict__ p,
+                                 double* __restrict__ sv, double* __restrict__ x,
+                                 double* __restrict__ r, double* __restrict__ u,
+                                 double* __restrict__ part) {
     __shared__ double sh[32];
-    double pq = sum_partials(partA, nb, 1, sh);
-    double rz = sum_partials(partB_prev, nb, 2, sh);
-    double alpha = pq != 0.0 ? rz / pq : 0.0;
-    double rzn = 0, rr = 0;
+    const double alpha = __ldcg(&cg[0]), beta = __ldcg(&cg[1]);
+    double g = 0, rr = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
-        double xi = x[i] + alpha * p[i];
-        double ri = r[i] - alpha * q[i];
-        double zi = dinv[i] * ri;
-        x[i] = xi;
+        const double pi = u[i] + beta * p[i];
+        const double si = w[i] + beta * sv[i];
+        const double ri = r[i] - alpha * si;
+        const double ui = dinv[i] * ri;
+        p[i] = pi;
+        sv[i] = si;
+        x[i] += alpha * pi;
         r[i] = ri;
-        z[i] = zi;
-        rzn += ri * zi;
+        u[i] = ui;
+        g += ri * ui;
         rr += ri * ri;
     }
-    double a = block_sum(rzn, sh);
-    double b = block_sum(rr, sh);
+    const double a = block_sum(g, sh);
+    const double b = block_sum(rr, sh);
     if (threadIdx.x == 0) {
-        partB_cur[blockIdx.x * 2] = a;
-        partB_cur[blockIdx.x * 2 + 1] = b;
+        part[3 * blockIdx.x + 0] = a;
+        part[3 * blockIdx.x + 2] = b;
     }
 }
 
-__global__ void pcg_dir_kernel(const double* __restrict__ partB_prev,
-                               const double* __restrict__ partB_cur, int nb, int64_t N,
-                               const double* __restrict__ z, double* __restrict__ p) {
+__global__ void partial_sum_kernel(const double* __restrict__ part, int nb, int stride, int off,
+                                   double* __restrict__ out) {
     __shared__ double sh[32];
-    double rzo = sum_partials(partB_prev, nb, 2, sh);
-    double rzn = sum_partials(partB_cur, nb, 2, sh);
-    double beta = rzo != 0.0 ? rzn / rzo : 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-         i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = z[i] + beta * p[i];
+    double v = 0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += part[(int64_t)b * stride + off];
+    const double t = block_sum(v, sh);
+    if (threadIdx.x == 0) *out = t;
 }
 
-__global__ void partial_final_kernel(const double* __restrict__ part, int nb, int stride, int off,
-                                     double* __restrict__ out) {
-    __shared__ double sh[32];
-    double v = sum_partials(part + off, nb, stride, sh);
-    if (threadIdx.x == 0) *out = v;
-}
-
-int pcg_solve(DeviceState& d, double rtol, int maxit, int* iters, double* rel_res,
-              cudaStream_t s) {
+int sell_build(DeviceState& d, int64_t* entries, int mixed, cudaStream_t s) {
     const int64_t N = d.N;
-    // memory-bound loops: enough resident warps (8 blocks of 8 warps per SM) to cover
-    // the dependent row_ptr -> col -> p[col] loads of the SpMV
+    const int64_t nslice = (N + 31) / 32;
     const int nb = 8 * num_sms();
-    double* partA = d.partials;
-    double* partB[2] = {d.partials + nb, d.partials + 3 * nb};
+    sell_count_kernel<<<nb, CG_THREADS, 0, s>>>(d.fcnt, d.fcol, d.fval, N, nslice, d.sell_w);
+    note_launch();
+    SDOT_CUDA_TRY(cudaGetLastError());
+    SDOT_CUDA_TRY(cudaMemsetAsync(d.sell_w + nslice, 0, 4, s));
+    int rc = scan_exclusive_i32_to_i64(d.sell_w, d.sell_ptr, nslice + 1, d.partials + 65536, s);
+    if (rc) return rc;
+    int64_t tot = 0;
+    SDOT_CUDA_TRY(cudaMemcpyAsync(&tot, d.sell_ptr + nslice, 8, cudaMemcpyDeviceToHost, s));
+    SDOT_CUDA_TRY(cudaStreamSynchronize(s));
+    *entries = 32 * tot;  // slice widths sum to tot; each slice holds 32 rows
+    (void)mixed;
+    return SDOT_OK;
+}
+
+__global__ void scale_ptr_kernel(int64_t* __restrict__ ptr, int64_t n) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) ptr[t] *= 32;
+}
+
+int sell_fill(DeviceState& d, int mixed, cudaStream_t s) {
+    const int64_t N = d.N;
+    const int64_t nslice = (N + 31) / 32;
+    const int nb = 8 * num_sms();
+    scale_ptr_kernel<<<(unsigned)((nslice + 1 + 255) / 256), 256, 0, s>>>(d.sell_ptr, nslice + 1);
+    note_launch();
+    SDOT_CUDA_TRY(cudaGetLastError());
+    if (mixed)
+        sell_fill_kernel<float><<<nb, CG_THREADS, 0, s>>>(d.fcnt, d.fcol, d.fval, N, nslice,
+                                                          d.sell_ptr, d.sell_col,
+                                                          (float*)d.sell_val, d.dinv);
+    else
+        sell_fill_kernel<double><<<nb, CG_THREADS, 0, s>>>(d.fcnt, d.fcol, d.fval, N, nslice,
+                                                           d.sell_ptr, d.sell_col,
+                                                           (double*)d.sell_val, d.dinv);
+    note_launch();
+    SDOT_CUDA_TRY(cudaGetLastError());
+    d.sell_mixed = mixed;
+    return SDOT_OK;
+}
+
+int cg_solve(DeviceState& d, double rtol, int maxit, int* iters, double* rel_res,
+             cudaStream_t s) {
+    const int64_t N = d.N;
+    const int64_t nslice = (N + 31) / 32;
+    // memory-bound loops: 8 blocks of 8 warps per SM keep enough loads in flight for
+    // the gathers of the SpMV
+    const int nb = 8 * num_sms();
+    double* part = d.partials;  // 3 per block
+    double* cg = d.scal + 16;   // scalars (see cg_spmv_kernel)
+    unsigned int* done = reinterpret_cast<unsigned int*>(d.scal + 32);
     double* hs = d.scal + 8;
-    // mean of g = nu - V (its sum is rounding noise when sum nu = |box|)
-    // computed on the host from the last evaluation reduction: scal[0] holds sum V
+    // mean of g = nu - V (its sum is rounding noise when sum nu = |box|), from the last
+    // evaluation's reduction: scal[0] holds sum V
     double sums[1];
     SDOT_CUDA_TRY(cudaMemcpyAsync(sums, d.scal, 8, cudaMemcpyDeviceToHost, s));
     SDOT_CUDA_TRY(cudaStreamSynchronize(s));
-    double box = d.L[0] * d.L[1] * d.L[2];
-    double mean = (box - sums[0]) / (double)N;
-    pcg_init_kernel<<<nb, PCG_THREADS, 0, s>>>(d.nu, d.vol, mean, d.dinv, N, d.x, d.r, d.z, d.p,
-                                               partB[1]);
-                                               note_launch();
-    SDOT_CUDA_TRY(cudaGetLastError());
-    double h[2];
-    partial_final_kernel<<<1, PCG_THREADS, 0, s>>>(partB[1], nb, 2, 1, hs);
+    const double box = d.L[0] * d.L[1] * d.L[2];
+    const double mean = (box - sums[0]) / (double)N;
+    SDOT_CUDA_TRY(cudaMemsetAsync(done, 0, sizeof(unsigned int), s));
+    cg_init_kernel<<<nb, CG_THREADS, 0, s>>>(d.nu, d.vol, mean, d.dinv, N, d.x, d.r, d.z, d.p,
+                                             d.sv, part, cg);
     note_launch();
-    SDOT_CUDA_TRY(cudaMemcpyAsync(h, hs, 8, cudaMemcpyDeviceToHost, s));
+    SDOT_CUDA_TRY(cudaGetLastError());
+    partial_sum_kernel<<<1, CG_THREADS, 0, s>>>(part, nb, 3, 2, hs);
+    note_launch();
+    double h = 0;
+    SDOT_CUDA_TRY(cudaMemcpyAsync(&h, hs, 8, cudaMemcpyDeviceToHost, s));
     SDOT_CUDA_TRY(cudaStreamSynchronize(s));
-    const double rr0 = h[0];
+    const double rr0 = h;
     *iters = 0;
     *rel_res = 0.0;
     if (!(rr0 > 0.0)) return SDOT_OK;
@@ -335,24 +483,29 @@ int pcg_solve(DeviceState& d, double rtol, int maxit, int* iters, double* rel_re
     const int check = 8;
     int it = 0;
     double rr = rr0;
+    // u lives in d.z and w in d.q
     while (it < maxit) {
         for (int c = 0; c < check && it < maxit; c++, it++) {
-            double* prev = partB[(it + 1) & 1];
-            double* cur = partB[it & 1];
-            pcg_spmv_kernel<<<nb, PCG_THREADS, 0, s>>>(d.row_ptr, d.col, d.val, d.p, N, d.q, partA);
+            if (d.sell_mixed)
+                cg_spmv_kernel<float><<<nb, CG_THREADS, 0, s>>>(
+                    d.sell_ptr, d.sell_col, (const float*)d.sell_val, N, nslice, d.z, d.q, part,
+                    done, cg);
+            else
+                cg_spmv_kernel<double><<<nb, CG_THREADS, 0, s>>>(
+                    d.sell_ptr, d.sell_col, (const double*)d.sell_val, N, nslice, d.z, d.q, part,
+                    done, cg);
             note_launch();
-            pcg_update_kernel<<<nb, PCG_THREADS, 0, s>>>(partA, prev, cur, nb, d.dinv, N, d.x, d.r,
-                                                         d.z, d.p, d.q);
-                                                         note_launch();
-            pcg_dir_kernel<<<nb, PCG_THREADS, 0, s>>>(prev, cur, nb, N, d.z, d.p);
+            cg_update_kernel<<<nb, CG_THREADS, 0, s>>>(cg, d.dinv, N, d.q, d.p, d.sv, d.x, d.r,
+                                                       d.z, part);
             note_launch();
         }
         SDOT_CUDA_TRY(cudaGetLastError());
-        partial_final_kernel<<<1, PCG_THREADS, 0, s>>>(partB[(it - 1) & 1], nb, 2, 1, hs);
+        // (r, r) after the last update
+        partial_sum_kernel<<<1, CG_THREADS, 0, s>>>(part, nb, 3, 2, hs);
         note_launch();
-        SDOT_CUDA_TRY(cudaMemcpyAsync(h, hs, 8, cudaMemcpyDeviceToHost, s));
+        SDOT_CUDA_TRY(cudaMemcpyAsync(&h, hs, 8, cudaMemcpyDeviceToHost, s));
         SDOT_CUDA_TRY(cudaStreamSynchronize(s));
-        rr = h[0];
+        rr = h;
         if (!(rr > thr)) break;
     }
     *iters = it;
@@ -385,6 +538,18 @@ __global__ void sum_kernel(const double* __restrict__ v, int64_t N, double* __re
         t += v[i];
     double a = block_sum(t, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = a;
+}
+
+// fixed-order sum of nb partials with stride; every block gets the same value
+__device__ __forceinline__ double sum_partials(const double* __restrict__ part, int nb, int stride,
+                                               double* sh) {
+    double v = 0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += part[(int64_t)b * stride];
+    const double t = block_sum(v, sh);
+    __shared__ double bc;
+    if (threadIdx.x == 0) bc = t;
+    __syncthreads();
+    return bc;
 }
 
 __global__ void sub_mean_kernel(double* __restrict__ v, int64_t N, const double* __restrict__ part,
