@@ -1,18 +1,16 @@
 """Benchmark: semi-discrete OT reconstruction on one GB300 (or N replicas).
 
 Setup (untimed for the step metric): a damped-Newton solve from psi = 0 to
-max|V - nu|/nu <= 10 tol on the workload box, which yields weights psi_a.
+max|V - nu|/nu <= tol on the workload box (timed as the OT solve), continued to tol/10.
 
-One step finishes the solve from there and so runs every row of the hot path:
-grid hash + kNN (sdot_create), damped Newton from psi_a to max|V - nu|/nu <= tol
-(Laguerre evaluations with the security test, re-queue and FP64 re-clip, reductions,
-Hessian CSR assembly, Jacobi PCG, line-search evaluations) and the displacement of
-every cell (sdot_displacement). Positions and psi_a are in device memory when the
-timed region starts; ``e2e`` repeats the measurement through the same C ABI with host
-buffers (positions and psi_a copied in, displacements out, inside the timed region).
-``ot_solve_s`` = setup time + one step = the OT solve time from psi = 0.
-
-value = cells per second through one such pass (N / step time), summed over ranks.
+A step is one Laguerre evaluation (sdot_laguerre: security test, re-queue and FP64
+re-clip passes, reductions, volumes, centroids and the CSR Hessian) at converged
+weights, kNN excluded: the cells/s definition of the measurement plan. value = N / mean
+step time, summed over ranks. Positions and weights are in device memory when the timed
+region starts; ``e2e`` repeats the calls through host buffers (psi in, volumes and
+centroids out, copied inside the timed region). ``extra.ot_solve_s`` holds the OT solve
+time from psi = 0 (sdot_create + sdot_solve to tol) in both precisions, measured in the
+same run.
 The default workload is the 256^3 Zel'dovich box with 5% clumped points (17.6 M
 seeds), mixed precision. ``--impl reference`` times the CPU oracle instead on a
 bounded sample of the same workload (certified cells at psi = 0, cells/s).
@@ -44,6 +42,14 @@ DEFAULT_WORKLOAD = "zeldovich-256^3-kinv-0.3a+clumps"
 FLOP_PER_CELL = 6000.0
 FP32_LANES_PER_SM = 128
 N_SM = 152
+# CG vector traffic per row and iteration: the update kernel reads u, p, w, s, x, r and
+# the inverse diagonal and writes p, s, x, r, u (96 B); the SpMV reads u_i and writes w_i
+# (16 B); the gathered neighbour values u_j are counted once per row (8 B)
+CG_BYTES_PER_ROW = 120
+# DRAM bytes per launch from an ncu capture of the current kernels (None: not captured
+# since the kernel last changed)
+CLIP_TRAFFIC = None
+CG_TRAFFIC = None
 
 
 def parse():
@@ -56,7 +62,7 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--tol", type=float, default=1e-4)
     ap.add_argument("--no-fp64-compare", action="store_true",
-                    help="skip the single FP64 solve reported beside the mixed one")
+                    help="skip the OT solve and evaluations in the other precision")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--laguerre-once", action="store_true",
@@ -162,29 +168,58 @@ def replica_config(workload, rank, world):
     return cfg
 
 
-def cpu_baseline(workload, cells=4):
-    """The CPU oracle as it stands, on a bounded sample of the workload's cells.
-
-    Each certified oracle cell sorts all N candidate seeds, so one sample is ``cells``
-    random cells of the box at psi = 0, one per host thread (OpenMP over cells).
-    """
+def _oracle_cells_worker(path, L, idx):
+    """One host core: the certified oracle cells idx of the box stored at path (psi = 0),
+    single-threaded. Returns the seconds it took."""
+    os.environ["OMP_NUM_THREADS"] = "1"
     sys.path.insert(0, os.path.join(ROOT, "oracle"))
     import sdot_oracle as O
+
+    y = np.load(path, mmap_mode="r")
+    y = np.ascontiguousarray(y)
+    psi = np.zeros(y.shape[0])
+    O.cells(y, psi, L, "certified", idx=np.asarray(idx[:1]))  # build / load first
+    t0 = time.perf_counter()
+    O.cells(y, psi, L, "certified", idx=np.asarray(idx))
+    return time.perf_counter() - t0
+
+
+_BASELINE_BOX = {}
+
+
+def cpu_baseline(workload, cells=None):
+    """The CPU oracle as it stands, on a bounded sample of the workload's cells.
+
+    Each certified oracle cell sorts all N candidate seeds, so one sample is one random
+    cell of the box at psi = 0 per host core, computed by single-threaded worker
+    processes (started with spawn) that share the positions through a memory-mapped
+    file. The rate is the sample's cells over the slowest worker's time.
+    """
+    import multiprocessing as mp
+    import tempfile
+
     from paper_2110_08868_gb300 import ics
 
-    y, nu, L = ics.make_config(**ics.CONFIGS[workload])
-    N = y.shape[0]
-    psi = np.zeros(N)
+    if workload not in _BASELINE_BOX:
+        y, nu, L = ics.make_config(**ics.CONFIGS[workload])
+        fd, path = tempfile.mkstemp(suffix=".npy")
+        os.close(fd)
+        np.save(path, y)
+        _BASELINE_BOX[workload] = (path, int(y.shape[0]), float(L))
+    path, N, L = _BASELINE_BOX[workload]
+    nproc = os.cpu_count() or 1
+    cells = cells or nproc
     rng = np.random.default_rng(123)
-    threads = min(cells, os.cpu_count() or 1)
     idx = rng.choice(N, cells, replace=False)
-    O.cells(y, psi, L, "certified", idx=idx[:1])  # load / build outside the timing
-    t0 = time.perf_counter()
-    O.cells(y, psi, L, "certified", idx=idx)
-    dt = time.perf_counter() - t0
-    return {"value": cells / dt, "unit": "cells/s", "cores": threads, "kind": "oracle",
+    parts = [idx[w::nproc].tolist() for w in range(min(nproc, cells))]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(len(parts)) as pool:
+        secs = pool.starmap(_oracle_cells_worker, [(path, L, part) for part in parts])
+    dt = max(secs)
+    return {"value": cells / dt, "unit": "cells/s", "cores": len(parts), "kind": "oracle",
             "sample": f"{cells} random certified oracle cells of the {workload} box (N={N}) at "
-                      f"psi=0, {dt:.1f} s on {threads} host threads"}
+                      f"psi=0 on {len(parts)} host cores (one single-threaded worker process "
+                      f"per core), slowest worker {dt:.1f} s"}
 
 
 def run_reference(args, rank, world):
@@ -210,175 +245,180 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def timed_solve(B, pos_dev, box, prec, tol):
+    """OT solve time from psi = 0: sdot_create (kNN) + sdot_solve(tol), wall clock with
+    the device synchronised on both sides. Returns (seconds, stats, ctx)."""
+    import torch
+
+    opt = B.sdot_default_options(precision=prec)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, ctx = B.sdot_create(pos_dev, None, box, opt)
+    B.check(rc)
+    st = B.sdot_stats()
+    B.check(B.sdot_solve(ctx, tol, None, st))
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0, st.as_dict(), ctx
+
+
+def eval_steps(B, ctx, psis, vol, cen, hcsr, n, stream):
+    """n evaluations (sdot_laguerre with volumes, centroids and the CSR Hessian) cycling
+    through psis; per call its device time (CUDA events on the context's stream) and the
+    library's report of the clipping passes."""
+    import torch
+
+    ms, info = [], []
+    for k in range(n):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        B.check(B.sdot_laguerre(ctx, psis[k % len(psis)], vol, cen, hcsr))
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        ei = B.sdot_eval_info()
+        B.check(B.sdot_last_eval(ctx, ei))
+        info.append(ei.as_dict())
+    return ms, info
+
+
 def run_native(args, rank, world, local):
     import torch
 
     from paper_2110_08868_gb300 import binding as B
-    from paper_2110_08868_gb300 import ics
 
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("gloo")
+    from paper_2110_08868_gb300 import ics
+
     y, nu, L = ics.make_config(**replica_config(args.workload, rank, world))
     N = int(y.shape[0])
     box = [L, L, L]
     pos_dev = torch.from_numpy(y).cuda()
-    disp_dev = torch.empty((N, 3), dtype=torch.float64, device="cuda")
-    opt = B.sdot_default_options(precision=args.precision)
     stream = torch.cuda.current_stream()
+    other = "fp64" if args.precision == "mixed" else "mixed"
 
-    # setup: solve from psi = 0 to 10 x tol; each step then finishes the solve from there
-    rc, ctx = B.sdot_create(pos_dev, None, box, opt)
-    B.check(rc)
-    st0 = B.sdot_stats()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    B.check(B.sdot_solve(ctx, 10.0 * args.tol, None, st0))
-    torch.cuda.synchronize()
-    setup_s = time.perf_counter() - t0
-    psi_dev = torch.empty(N, dtype=torch.float64, device="cuda")
-    B.check(B.sdot_get_psi(ctx, psi_dev))
-    B.sdot_destroy(ctx)
-    solve_stats = st0.as_dict()
-    step_tol = args.tol
-    step_opt = B.sdot_default_options(precision=args.precision)
-
-    def one_step(pos, disp, psi0, o=step_opt):
-        rc, ctx = B.sdot_create(pos, None, box, o)
-        B.check(rc)
-        try:
-            st = B.sdot_stats()
-            B.check(B.sdot_solve(ctx, step_tol, psi0, st))
-            B.check(B.sdot_displacement(ctx, disp))
-        finally:
-            B.sdot_destroy(ctx)
-        return st
-
-    def barrier():
+    # OT solve from psi = 0 in the bench precision; its weights psi_a (max|V - nu|/nu <=
+    # tol) and their continuation psi_b (<= tol/10) are the converged weights at which
+    # the evaluations are timed. The timed calls alternate between the two, so every
+    # call computes a new diagram from the previous one (the solver's access pattern).
+    solve_s, solve_st, ctx = timed_solve(B, pos_dev, box, args.precision, args.tol)
+    try:
+        psi_a = torch.empty(N, dtype=torch.float64, device="cuda")
+        psi_b = torch.empty(N, dtype=torch.float64, device="cuda")
+        B.check(B.sdot_get_psi(ctx, psi_a))
+        st_b = B.sdot_stats()
+        B.check(B.sdot_solve(ctx, 0.1 * args.tol, psi_a, st_b))
+        B.check(B.sdot_get_psi(ctx, psi_b))
+        vol = torch.empty(N, dtype=torch.float64, device="cuda")
+        cen = torch.empty((N, 3), dtype=torch.float64, device="cuda")
+        hcsr = B.sdot_csr()
+        psis = [psi_a, psi_b]
+        eval_steps(B, ctx, psis, vol, cen, hcsr, args.warmup, stream)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local)
+        sampler.start()
         if dist is not None:
             dist.barrier()
-
-    # warm-up
-    for _ in range(args.warmup):
-        one_step(pos_dev, disp_dev, psi_dev)
-    torch.cuda.synchronize()
-    sampler = ClockSampler(local)
-    sampler.start()
-    barrier()
-    torch.cuda.synchronize()
-    l0 = B.sdot_kernel_launches()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    stats = []
-    for _ in range(args.steps):
-        stats.append(one_step(pos_dev, disp_dev, psi_dev).as_dict())
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    launches = B.sdot_kernel_launches() - l0
-    clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    ms_max = max_over_ranks(ms, dist)
-    value = world * N / (ms_max / 1e3)
-
-    # e2e through host buffers (pinned), copies inside the timed region
-    e2e = None
-    if not args.no_e2e:
-        pos_host = torch.from_numpy(y).pin_memory()
-        psi_host = psi_dev.cpu().pin_memory()
-        disp_host = torch.empty((N, 3), dtype=torch.float64).pin_memory()
-        barrier()
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            one_step(pos_host, disp_host, psi_host)
+        l0 = B.sdot_kernel_launches()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        ms_each, info = eval_steps(B, ctx, psis, vol, cen, hcsr, args.steps, stream)
+        ev1.record(stream)
         torch.cuda.synchronize()
-        e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps, dist)
-        e2e = {"value": world * N / (e_ms / 1e3), "unit": "cells/s",
-               "h2d_bytes_per_step": N * 3 * 8 + N * 8, "d2h_bytes_per_step": N * 3 * 8}
+        if dist is not None:
+            dist.barrier()
+        launches = B.sdot_kernel_launches() - l0
+        clocks = sampler.stop()
+        ms = ev0.elapsed_time(ev1) / args.steps
+        ms_max = max_over_ranks(ms, dist)
+        value = world * N / (ms_max / 1e3)
+        hess_nnz = int(hcsr.nnz)
+
+        # e2e: the same calls through pinned host buffers (psi in, volumes and centroids
+        # out, the copies inside the timed region)
+        e2e = None
+        if not args.no_e2e:
+            psis_h = [p.cpu().pin_memory() for p in psis]
+            vol_h = torch.empty(N, dtype=torch.float64).pin_memory()
+            cen_h = torch.empty((N, 3), dtype=torch.float64).pin_memory()
+            if dist is not None:
+                dist.barrier()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for k in range(args.steps):
+                B.check(B.sdot_laguerre(ctx, psis_h[k % 2], vol_h, cen_h, hcsr))
+            torch.cuda.synchronize()
+            e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps, dist)
+            e2e = {"value": world * N / (e_ms / 1e3), "unit": "cells/s",
+                   "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N + 24 * N}
+    finally:
+        B.sdot_destroy(ctx)
 
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
 
-    st = stats[-1]
-    if args.precision == "mixed":
-        n1 = sum(x["evals_fp32"] for x in stats)
-        pass1_ms = sum(x["ms_pass1_fp32"] for x in stats) / max(n1, 1)
-    else:
-        n1 = sum(x["laguerre_evals"] for x in stats)
-        pass1_ms = sum(x["ms_pass"][0] for x in stats) / max(n1, 1)
     peaks = measured_peaks()
+    # clip roofline: the first clipping pass of each timed evaluation
+    pass1 = [x["ms_pass"][0] for x in info]
+    pass1_ms = statistics.median(pass1)
     clock_ghz = (clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)) / 1e3
     peak_tf = N_SM * FP32_LANES_PER_SM * 2 * clock_ghz / 1e3
     achieved_tf = N * FLOP_PER_CELL / (pass1_ms / 1e3) / 1e12
-    roofline = {"kernel": "clip_kernel<float,certify> (first clipping pass)" if args.precision ==
-                "mixed" else "clip_kernel<double,certify> (first clipping pass)", "bound": "alu",
-                "launches_timed": n1,
-                "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
-                "frac": achieved_tf / peak_tf, "traffic": None,
-                "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {clock_ghz:.3f} GHz "
-                               "(median SM clock sampled under load)",
+    kname = "clip_kernel<float,CapS,certify>" if args.precision == "mixed" else \
+        "clip_kernel<double,CapS,certify>"
+    roofline = {"kernel": kname + " (first clipping pass)", "bound": "alu",
+                "launches_timed": len(pass1), "achieved": achieved_tf, "peak": peak_tf,
+                "unit": "TFLOP/s", "frac": achieved_tf / peak_tf, "traffic": CLIP_TRAFFIC,
+                "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {clock_ghz:.3f} "
+                               "GHz (median SM clock sampled under load)",
                 "per_launch_ms": pass1_ms, "flop_per_cell": FLOP_PER_CELL}
-    # PCG (HBM-bound): algorithmic bytes per iteration = SpMV (12 B per nonzero + row
-    # pointers + gathered p) + the fused vector updates (~9 doubles per row)
-    nnz_est = 17.0 * N
-    spmv = None
-    if st["cg_iters"] > 0:
-        it_ms = st["ms_cg"] / st["cg_iters"]
-        bytes_it = 12.0 * nnz_est + 8.0 * (N + 1) + 8.0 * 9 * N
+    # CG (HBM-bound): algorithmic bytes per iteration = the stored sliced-ELL entries
+    # (int32 column + weight) + the vectors (see CG_BYTES_PER_ROW)
+    cg = None
+    if solve_st["cg_iters"] > 0:
+        it_ms = solve_st["ms_cg"] / solve_st["cg_iters"]
+        wbytes = 4 if args.precision == "mixed" else 8
+        bytes_it = solve_st["hess_slots"] * (4 + wbytes) + CG_BYTES_PER_ROW * N
         gbs = bytes_it / (it_ms / 1e3) / 1e9
-        hbm = peaks.get("hbm_gbs", 6779.0)
-        spmv = {"kernel": "PCG iteration (spmv + update + direction)", "bound": "hbm",
-                "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                "traffic": None, "per_iter_ms": it_ms,
-                "bytes_per_iter": bytes_it, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
-    # OT solve time from psi = 0: the setup part (to 10 tol) plus one step (to tol)
-    extra = {"ot_solve_s": {args.precision: setup_s + ms_max / 1e3},
-             "solve": {k: solve_stats[k] for k in ("newton_iters", "laguerre_evals", "cg_iters",
-                                                   "max_rel_err", "ms_knn", "ms_clip", "ms_cg",
-                                                   "ms_pass")},
-             "step": {k: st[k] for k in ("newton_iters", "laguerre_evals", "cg_iters",
-                                         "requeued", "reclipped_fp64", "ms_knn", "ms_clip",
-                                         "ms_cg", "ms_total", "ms_pass", "refined_fp64",
-                                         "max_rel_err")},
-             "roofline_pcg": spmv}
-    # one Laguerre evaluation at psi_a on a warm context (clip, re-queue, FP64 re-clip,
-    # reductions and the CSR Hessian; kNN and Newton excluded): cells/s per evaluation
-    try:
-        rc, ctx = B.sdot_create(pos_dev, None, box, opt)
-        B.check(rc)
+        hbm = peaks.get("hbm_gbs", 6786.2)
+        cg = {"kernel": "CG iteration (cg_spmv_kernel + cg_update_kernel)", "bound": "hbm",
+              "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+              "traffic": CG_TRAFFIC, "per_iter_ms": it_ms, "bytes_per_iter": bytes_it,
+              "hess_slots": solve_st["hess_slots"], "hess_offdiag": solve_st["hess_offdiag"],
+              "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    keep = ("newton_iters", "laguerre_evals", "cg_iters", "max_rel_err", "ms_knn", "ms_clip",
+            "ms_cg", "ms_pass", "refined_fp64")
+    extra = {"ot_solve_s": {args.precision: solve_s},
+             "solve": {args.precision: {k: solve_st[k] for k in keep}},
+             "eval_ms_median": statistics.median(ms_each),
+             "cells_per_s_median": N / (statistics.median(ms_each) / 1e3),
+             "eval_detail": {"requeued": [x["requeued"] for x in info][:4],
+                             "reclipped_fp64": [x["reclipped_fp64"] for x in info][:4],
+                             "ms_pass_median": [statistics.median(x["ms_pass"][q] for x in info)
+                                                for q in range(3)]},
+             "hess_nnz": hess_nnz,
+             "roofline_cg": cg}
+    if not args.no_fp64_compare:
+        # the other precision: its OT solve from psi = 0 in the same run, and its cells/s
+        # at the same two converged weights
+        s2, st2, ctx2 = timed_solve(B, pos_dev, box, other, args.tol)
         try:
-            vol_dev = torch.empty(N, dtype=torch.float64, device="cuda")
-            hcsr = B.sdot_csr()
-            B.check(B.sdot_laguerre(ctx, psi_dev, vol_dev, None, hcsr))  # first diagram
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            B.check(B.sdot_laguerre(ctx, None, vol_dev, None, hcsr))  # warm: previous facets
-            torch.cuda.synchronize()
-            lag_ms = (time.perf_counter() - t0) * 1e3
+            eval_steps(B, ctx2, psis, vol, cen, hcsr, 2, stream)
+            ms2, info2 = eval_steps(B, ctx2, psis, vol, cen, hcsr, 4, stream)
         finally:
-            B.sdot_destroy(ctx)
-        extra["laguerre_eval"] = {"ms": lag_ms, "cells_per_s": N / (lag_ms / 1e3),
-                                  "what": "one sdot_laguerre at psi_a with the CSR Hessian, "
-                                          "warm context, device buffers"}
-    except Exception as e:  # reported, never fatal to the bench line
-        extra["laguerre_eval"] = {"error": str(e)[:200]}
-    if not args.no_fp64_compare and args.precision == "mixed":
-        opt64 = B.sdot_default_options(precision="fp64")
-        one_step(pos_dev, disp_dev, psi_dev, opt64)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        s64 = one_step(pos_dev, disp_dev, psi_dev, opt64).as_dict()
-        torch.cuda.synchronize()
-        extra["fp64_step_ms"] = (time.perf_counter() - t0) * 1e3
-        extra["fp64_step"] = {k: s64[k] for k in ("laguerre_evals", "ms_clip", "ms_cg",
-                                                  "ms_pass")}
-        extra["mixed_step_ms"] = ms_max
+            B.sdot_destroy(ctx2)
+        extra["ot_solve_s"][other] = s2
+        extra["solve"][other] = {k: st2[k] for k in keep}
+        extra["cells_per_s_" + other] = N / (statistics.median(ms2) / 1e3)
+        extra["mixed_solve_faster"] = extra["ot_solve_s"]["mixed"] < extra["ot_solve_s"]["fp64"]
     cpu = None
     if not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload)
@@ -388,8 +428,9 @@ def run_native(args, rank, world, local):
             "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": args.workload, "N": N, "precision": args.precision,
                        "tol": args.tol, "k": 24,
-                       "step": "kNN create + damped Newton from the 10 tol iterate to tol + "
-                               "displacement",
+                       "step": "one sdot_laguerre (volumes, centroids, CSR Hessian) at the "
+                               "converged weights of the solve to tol, alternating with its "
+                               "continuation to tol/10; kNN excluded",
                        "l2": "inputs larger than L2 (device working set >> 129 MB)",
                        "parallelism": "replicas" if world > 1 else "1 GPU"},
             "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "roofline": roofline,

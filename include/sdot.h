@@ -100,7 +100,24 @@ typedef struct {
     int refined_fp64;        /* 1 if a mixed-precision solve finished with FP64 evaluations */
     int evals_fp32;          /* evaluations with FP32 clipping */
     double ms_pass1_fp32;    /* device time of their first (security-test) pass */
+    int64_t hess_slots;      /* stored entries of the last Newton matrix (sliced-ELL:
+                                each slice of 32 rows padded to its longest row) */
+    int64_t hess_offdiag;    /* its nonzero off-diagonal entries */
 } sdot_stats;
+
+/* The last Laguerre evaluation of a context (sdot_laguerre or the last one of
+ * sdot_solve). */
+typedef struct {
+    double ms_clip;          /* device time of the clipping passes */
+    double ms_pass[3];       /* security-test pass, re-queue pass, FP64 re-clip pass */
+    int64_t requeued;        /* cells re-queued by the security test */
+    int64_t reclipped_fp64;  /* cells re-clipped in FP64 */
+    int64_t n_empty;         /* empty cells */
+    double max_rel_err;      /* max_j |V_j - nu_j| / nu_j */
+    double l2_err;           /* ||V - nu||_2 */
+    double min_vol;          /* min_j V_j */
+    int precision;           /* SDOT_PREC_* of the clipping */
+} sdot_eval_info;
 
 typedef struct sdot_ctx sdot_ctx;
 
@@ -188,7 +205,10 @@ int sdot_knn(sdot_ctx* ctx, int32_t* nbr);
 /* Per-cell status of the last evaluation (N bytes out, caller order). Bits:
  * 1 empty, 2 capacity exceeded, 4 failed the FP32 consistency check (then
  * re-clipped in FP64), 8 re-queued by the security test, 16 reaches a non-minimum
- * periodic image, 32/64/128 capacity detail (polytope / face / traversal stack). */
+ * periodic image, 32/64/128 capacity detail (polytope / face / traversal stack).
+ * A cell that went through the re-queue pass keeps bit 8, and a cell re-clipped in FP64
+ * with the large polytope keeps the bits that sent it there (4, or 32/64/128 when the
+ * small polytope overflowed); 1, 2 and 16 describe the final result. */
 int sdot_cell_status(sdot_ctx* ctx, uint8_t* status);
 
 /*
@@ -204,7 +224,7 @@ int sdot_cell_status(sdot_ctx* ctx, uint8_t* status);
  *  nbr:    N x k int32 out, device (or managed) memory; same contents as sdot_knn.
  *  stream: cudaStream_t for the work (NULL: legacy default stream); the call returns
  *          after synchronising it.
- * All scratch lives in one fixed array of about 6 MB declared in the library, which
+ * All scratch lives in one fixed array of about 7 MB declared in the library, which
  * every GPU that loads the library keeps until the process exits. The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress), so make that
  * first call before any stream capture. Calls share the array and it keeps the last
@@ -214,6 +234,9 @@ int sdot_cell_status(sdot_ctx* ctx, uint8_t* status);
 #define SDOT_STATIC_MAX_K 32
 int sdot_knn_static(const double* pos, int64_t N, const double box[3], int k, int32_t* nbr,
                     void* stream);
+
+/* Statistics of the context's last Laguerre evaluation (host memory out). */
+int sdot_last_eval(const sdot_ctx* ctx, sdot_eval_info* info);
 
 /* Number of seeds and kNN size of the context. */
 int sdot_size(const sdot_ctx* ctx, int64_t* N, int* k);

@@ -53,7 +53,21 @@ class sdot_stats(ctypes.Structure):
                 ("ms_clip", ctypes.c_double), ("ms_cg", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("ms_pass", ctypes.c_double * 3),
                 ("refined_fp64", ctypes.c_int), ("evals_fp32", ctypes.c_int),
-                ("ms_pass1_fp32", ctypes.c_double)]
+                ("ms_pass1_fp32", ctypes.c_double), ("hess_slots", ctypes.c_int64),
+                ("hess_offdiag", ctypes.c_int64)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["ms_pass"] = list(self.ms_pass)
+        return d
+
+
+class sdot_eval_info(ctypes.Structure):
+    _fields_ = [("ms_clip", ctypes.c_double), ("ms_pass", ctypes.c_double * 3),
+                ("requeued", ctypes.c_int64), ("reclipped_fp64", ctypes.c_int64),
+                ("n_empty", ctypes.c_int64), ("max_rel_err", ctypes.c_double),
+                ("l2_err", ctypes.c_double), ("min_vol", ctypes.c_double),
+                ("precision", ctypes.c_int)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -81,7 +95,7 @@ class sdot_server_info(ctypes.Structure):
 EXPORTS = ["sdot_default_options", "sdot_create", "sdot_set_stream", "sdot_set_allocator",
            "sdot_laguerre",
            "sdot_solve", "sdot_csr_copy", "sdot_get_psi", "sdot_displacement", "sdot_knn",
-           "sdot_cell_status", "sdot_knn_static", "sdot_size", "sdot_destroy",
+           "sdot_cell_status", "sdot_knn_static", "sdot_last_eval", "sdot_size", "sdot_destroy",
            "sdot_kernel_launches", "sdot_last_error",
            "sdot_server_default_options", "sdot_server_footprint", "sdot_server_create",
            "sdot_server_submit", "sdot_server_poll", "sdot_server_wait", "sdot_server_result",
@@ -124,6 +138,7 @@ def load(path=LIB_PATH):
     lib.sdot_cell_status.argtypes = [P, P]
     lib.sdot_knn_static.argtypes = [P, I64, P, I, P, P]
     lib.sdot_size.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I)]
+    lib.sdot_last_eval.argtypes = [P, ctypes.POINTER(sdot_eval_info)]
     lib.sdot_destroy.argtypes = [P]
     lib.sdot_destroy.restype = None
     lib.sdot_kernel_launches.argtypes = []
@@ -275,6 +290,10 @@ def sdot_knn_static(pos, box, k, nbr, stream=None):
     h = getattr(stream, "cuda_stream", stream)
     return load().sdot_knn_static(_ptr(pos), int(pos.shape[0]), ctypes.c_void_p(b.ctypes.data),
                                   int(k), _ptr(nbr, np.int32), ctypes.c_void_p(h) if h else None)
+
+
+def sdot_last_eval(ctx, info):
+    return load().sdot_last_eval(ctx, ctypes.byref(info))
 
 
 def sdot_size(ctx):

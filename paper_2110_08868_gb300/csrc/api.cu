@@ -48,6 +48,9 @@ struct sdot_ctx {
     bool eval_valid = false;  // last evaluation is at d.psi
     float ms_knn = 0;
     EvalResult last{};
+    int last_prec = SDOT_PREC_MIXED;  // precision of the last evaluation
+    int64_t sell_entries = 0;         // stored entries of the last Newton matrix
+    int64_t sell_offdiag = 0;         // its nonzero off-diagonal entries
     bool dry = false;         // allocation plan only: count bytes, allocate nothing
     size_t bytes = 0;         // device bytes requested by the allocations so far
     EvalHook eval_hook = nullptr;  // the server's batcher, or null: evaluate_cells
@@ -135,6 +138,9 @@ int eval_at(sdot_ctx* c, const double* psi_sorted, EvalResult* r, int precision 
     int rc = c->eval_hook ? c->eval_hook(c->eval_user, &c->d, psi_sorted, prec, r, c->stream)
                           : evaluate_cells(c->d, psi_sorted, prec, r, c->stream);
     if (rc) return rc;
+    c->last = *r;
+    c->last_prec = prec;
+    c->eval_valid = true;
     return SDOT_OK;
 }
 
@@ -184,9 +190,11 @@ int build_csr(sdot_ctx* c) {
 // the sliced-ELL Newton matrix: count, grow the arrays if needed (8 bytes of value per
 // entry, enough for either precision), fill
 int build_sell(sdot_ctx* c, int mixed) {
-    int64_t ent = 0;
-    int rc = sell_build(c->d, &ent, mixed, c->stream);
+    int64_t ent = 0, offd = 0;
+    int rc = sell_build(c->d, &ent, &offd, c->stream);
     if (rc) return rc;
+    c->sell_entries = ent;
+    c->sell_offdiag = offd;
     if (ent > c->sell_cap) {
         dev_free(c, c->d.sell_col);
         dev_free(c, c->d.sell_val);
@@ -482,6 +490,28 @@ int sdot_set_stream(sdot_ctx* c, void* stream) {
     return SDOT_OK;
 }
 
+int sdot_last_eval(const sdot_ctx* c, sdot_eval_info* info) {
+    if (!c || !info) {
+        set_error("sdot_last_eval: need a context and info");
+        return SDOT_ERR_ARG;
+    }
+    if (!c->eval_valid) {
+        set_error("sdot_last_eval: the context has not been evaluated yet");
+        return SDOT_ERR_ARG;
+    }
+    const EvalResult& r = c->last;
+    info->ms_clip = r.ms;
+    for (int q = 0; q < 3; q++) info->ms_pass[q] = r.ms_pass[q];
+    info->requeued = r.requeued;
+    info->reclipped_fp64 = r.reclipped;
+    info->n_empty = r.n_empty;
+    info->max_rel_err = r.max_rel_err;
+    info->l2_err = r.l2_err;
+    info->min_vol = r.min_vol;
+    info->precision = c->last_prec;
+    return SDOT_OK;
+}
+
 int sdot_size(const sdot_ctx* c, int64_t* N, int* k) {
     if (!c) return SDOT_ERR_ARG;
     if (N) *N = c->d.N;
@@ -705,6 +735,8 @@ int sdot_solve(sdot_ctx* c, double tol, const double* psi0, sdot_stats* st) {
     c->last = ev;
     c->eval_valid = true;
     S.newton_iters = it;
+    S.hess_slots = c->sell_entries;
+    S.hess_offdiag = c->sell_offdiag;
     S.max_rel_err = ev.max_rel_err;
     S.l2_err = ev.l2_err;
     S.min_vol = ev.min_vol;

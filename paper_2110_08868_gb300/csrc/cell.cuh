@@ -1552,7 +1552,15 @@ __device__ __forceinline__ void process_cell(Poly<R, C>& P, const ClipParams& cp
             cp.m1[3 * i] = cp.m1[3 * i + 1] = cp.m1[3 * i + 2] = 0.0;
         }
         if (st & (CS_EMPTY | CS_CAPACITY | CS_INCONSISTENT)) cp.topo_n[i] = 0;
-        cp.status[i] = (uint8_t)st;
+        // history of the evaluation kept in the final status: a cell of the re-queue
+        // pass was re-queued (8); a cell of the FP64 re-clip keeps what sent it there
+        // (4: FP32 check failed, 32/64/128: small capacity exceeded) and its re-queue
+        uint32_t hist = 0;
+        if (MODE == MODE_FULL && !BIG) hist = CS_UNCERTIFIED;
+        if (BIG)
+            hist = cp.status[i] & (CS_INCONSISTENT | CS_UNCERTIFIED | CS_CAP_POLY | CS_CAP_FACE |
+                                   CS_CAP_STACK);
+        cp.status[i] = (uint8_t)(st | hist);
         // FP32 cells failing a check, and cells over the small capacity, are clipped
         // again in FP64 with the large capacity
         const bool redo = !BIG && (((sizeof(R) == 4) && (st & CS_INCONSISTENT)) ||

@@ -340,26 +340,24 @@ struct TopK {
     }
 };
 
+// Exact search of query q: rings of grid cells with the FP64 key, from ring 0 until
+// the k-th key is below the squared distance to the first unvisited ring (brute force
+// over all seeds when the rings would wrap onto visited cells).
 template <int K>
-__global__ void __launch_bounds__(128) knn_kernel(const Pos4* __restrict__ pos,
-                                                  const int32_t* __restrict__ cell_start,
-                                                  KnnParams p, int32_t* __restrict__ knn,
-                                                  double* __restrict__ d2k,
-                                                  int* __restrict__ flags) {
-    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= p.N) return;
+__device__ __noinline__ void knn_exact(const Pos4* __restrict__ pos,
+                                       const int32_t* __restrict__ cell_start,
+                                       const KnnParams& p, int64_t q, TopK<K>& top) {
     const Pos4 yi = pos[q];
-    TopK<K> top;
     top.init();
     int c[3];
     double m = DBL_MAX;
     {
-        double xs[3] = {yi.x, yi.y, yi.z};
+        const double xs[3] = {yi.x, yi.y, yi.z};
         for (int a = 0; a < 3; a++) {
             int cc = (int)floor(xs[a] / p.h[a]);
             cc = cc < 0 ? 0 : (cc >= p.G[a] ? p.G[a] - 1 : cc);
             c[a] = cc;
-            double f = xs[a] - cc * p.h[a];
+            const double f = xs[a] - cc * p.h[a];
             double ma = fmin(f, p.h[a] - f);
             if (ma < 0) ma = 0;
             m = fmin(m, ma);
@@ -374,27 +372,24 @@ __global__ void __launch_bounds__(128) knn_kernel(const Pos4* __restrict__ pos,
             top.init();
             for (int64_t t = 0; t < p.N; t++) {
                 if (t == q) continue;
-                Pos4 yj = pos[t];
+                const Pos4 yj = pos[t];
                 top.insert(dist2_exact(yi, yj, p), (int)yj.w, (int)t);
             }
             break;
         }
         for (int oz = -r; oz <= r; oz++) {
-            int cz = c[2] + oz;
-            cz = (cz % p.G[2] + p.G[2]) % p.G[2];
+            const int cz = ((c[2] + oz) % p.G[2] + p.G[2]) % p.G[2];
             for (int oy = -r; oy <= r; oy++) {
-                int cy = c[1] + oy;
-                cy = (cy % p.G[1] + p.G[1]) % p.G[1];
-                bool face = (oz == -r || oz == r || oy == -r || oy == r);
-                int step = (face || r == 0) ? 1 : 2 * r;
+                const int cy = ((c[1] + oy) % p.G[1] + p.G[1]) % p.G[1];
+                const bool face = (oz == -r || oz == r || oy == -r || oy == r);
+                const int step = (face || r == 0) ? 1 : 2 * r;
                 for (int ox = -r; ox <= r; ox += step) {
-                    int cx = c[0] + ox;
-                    cx = (cx % p.G[0] + p.G[0]) % p.G[0];
-                    int64_t cell = ((int64_t)cz * p.G[1] + cy) * p.G[0] + cx;
-                    int32_t b = cell_start[cell], e = cell_start[cell + 1];
+                    const int cx = ((c[0] + ox) % p.G[0] + p.G[0]) % p.G[0];
+                    const int64_t cell = ((int64_t)cz * p.G[1] + cy) * p.G[0] + cx;
+                    const int32_t b = cell_start[cell], e = cell_start[cell + 1];
                     for (int32_t t = b; t < e; t++) {
                         if (t == q) continue;
-                        Pos4 yj = pos[t];
+                        const Pos4 yj = pos[t];
                         top.insert(dist2_exact(yi, yj, p), (int)yj.w, t);
                     }
                 }
@@ -408,6 +403,149 @@ __global__ void __launch_bounds__(128) knn_kernel(const Pos4* __restrict__ pos,
         for (int t = 0; t < K; t++)
             if (t == k - 1) kth = top.d[t];
         if (kth < DBL_MAX && kth < bound * bound * (1.0 - 1e-12)) done = true;
+    }
+}
+
+// Grid-local FP32 offsets of every seed (in units of the grid cell) and its grid cell,
+// for the FP32 pass of the search.
+__global__ void knn_prep_kernel(const Pos4* __restrict__ pos, int64_t N, KnnParams p,
+                                float4* __restrict__ off, int32_t* __restrict__ cellc) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N) return;
+    const Pos4 y = pos[t];
+    const double xs[3] = {y.x, y.y, y.z};
+    int c[3];
+    float o[3];
+    for (int a = 0; a < 3; a++) {
+        int cc = (int)floor(xs[a] / p.h[a]);
+        cc = cc < 0 ? 0 : (cc >= p.G[a] ? p.G[a] - 1 : cc);
+        c[a] = cc;
+        o[a] = (float)((xs[a] - cc * p.h[a]) / p.h[a]);
+    }
+    off[t] = make_float4(o[0], o[1], o[2], 0.f);
+    cellc[t] = c[0] | (c[1] << 10) | (c[2] << 20);
+}
+
+// k nearest seeds of every query. A first pass in FP32 keeps the K + 8 smallest
+// approximate squared distances (grid-cell difference plus FP32 offset difference, in
+// grid-cell units, minimum image); its error is below Delta = 1e-5 (F_k + 1) for
+// distances of a few grid cells, so every seed of the exact top k has an approximate
+// key <= tau = F_k + 2 Delta (F_k: the k-th approximate key). The rings stop once the
+// unvisited seeds are beyond tau + Delta. The entries <= tau then get the exact FP64 key
+// (no FMA, ties by caller index) and are ranked exactly. If the K + 8 entries do not
+// all fit below tau (many near ties, as on a lattice), the query takes the exact
+// search instead. FAST = false (k > 24, where the unrolled lists would cost more
+// registers than they save): the exact search for every query.
+template <int K, bool FAST>
+__global__ void __launch_bounds__(128) knn_kernel(const Pos4* __restrict__ pos,
+                                                  const float4* __restrict__ off,
+                                                  const int32_t* __restrict__ cellc,
+                                                  const int32_t* __restrict__ cell_start,
+                                                  KnnParams p, int32_t* __restrict__ knn,
+                                                  double* __restrict__ d2k,
+                                                  int* __restrict__ flags) {
+    constexpr int K2 = K + 8;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= p.N) return;
+    const int k = p.k;
+    if (!FAST) {  // large k: the exact search only
+        TopK<K> top;
+        knn_exact<K>(pos, cell_start, p, q, top);
+#pragma unroll
+        for (int t = 0; t < K; t++) {
+            if (t < k) knn[q * k + t] = top.s[t];
+            if (t == k - 1) d2k[q] = top.d[t];
+        }
+        if (top.d[0] == 0.0) atomicOr(flags, 1);
+        if (top.s[0] < 0) atomicOr(flags, 2);
+        return;
+    }
+    const float4 oi = off[q];
+    const int lc = cellc[q];
+    const int c[3] = {lc & 1023, (lc >> 10) & 1023, (lc >> 20) & 1023};
+    const float G[3] = {(float)p.G[0], (float)p.G[1], (float)p.G[2]};
+    // grid cells are near-cubic; distances in units of the x cell size
+    const float sy = (float)(p.h[1] / p.h[0]), sz = (float)(p.h[2] / p.h[0]);
+    float fd[K2];
+    int fi[K2];
+#pragma unroll
+    for (int t = 0; t < K2; t++) {
+        fd[t] = FLT_MAX;
+        fi[t] = -1;
+    }
+    const float m = fminf(fminf(fminf(oi.x, 1.f - oi.x), fminf(oi.y, 1.f - oi.y) * sy),
+                          fminf(oi.z, 1.f - oi.z) * sz);
+    const int Gmin = min(p.G[0], min(p.G[1], p.G[2]));
+    bool ok = false;
+    float tau = FLT_MAX;
+    for (int r = 0;; r++) {
+        if (2 * r + 1 > Gmin) break;  // rings would wrap: exact search
+        for (int oz = -r; oz <= r; oz++) {
+            const int cz = ((c[2] + oz) % p.G[2] + p.G[2]) % p.G[2];
+            for (int oy = -r; oy <= r; oy++) {
+                const int cy = ((c[1] + oy) % p.G[1] + p.G[1]) % p.G[1];
+                const bool face = (oz == -r || oz == r || oy == -r || oy == r);
+                const int step = (face || r == 0) ? 1 : 2 * r;
+                for (int ox = -r; ox <= r; ox += step) {
+                    const int cx = ((c[0] + ox) % p.G[0] + p.G[0]) % p.G[0];
+                    const int64_t cell = ((int64_t)cz * p.G[1] + cy) * p.G[0] + cx;
+                    const int32_t b = cell_start[cell], e = cell_start[cell + 1];
+                    for (int32_t t = b; t < e; t++) {
+                        if (t == q) continue;
+                        const float4 oj = off[t];
+                        float dx = (float)ox + (oj.x - oi.x);
+                        float dy = (float)oy + (oj.y - oi.y);
+                        float dz = (float)oz + (oj.z - oi.z);
+                        if (dx > 0.5f * G[0]) dx -= G[0];
+                        else if (dx < -0.5f * G[0]) dx += G[0];
+                        if (dy > 0.5f * G[1]) dy -= G[1];
+                        else if (dy < -0.5f * G[1]) dy += G[1];
+                        if (dz > 0.5f * G[2]) dz -= G[2];
+                        else if (dz < -0.5f * G[2]) dz += G[2];
+                        dy *= sy;
+                        dz *= sz;
+                        const float d2 = dx * dx + dy * dy + dz * dz;
+                        if (d2 < fd[K2 - 1]) {
+#pragma unroll
+                            for (int u = K2 - 1; u >= 0; u--) {
+                                if (d2 < fd[u]) {
+                                    const bool sh = u > 0 && d2 < fd[u - 1];
+                                    fd[u] = sh ? fd[u - 1] : d2;
+                                    fi[u] = sh ? fi[u - 1] : t;
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        float Fk = FLT_MAX;
+#pragma unroll
+        for (int t = 0; t < K2; t++)
+            if (t == k - 1) Fk = fd[t];
+        if (Fk == FLT_MAX) continue;
+        const float delta = 1e-5f * (Fk + 1.f);
+        tau = Fk + 2.f * delta;
+        // every unvisited seed lies at least r + m cell sizes away
+        const float bound = fminf((float)r * fminf(1.f, fminf(sy, sz)) + m, 1e30f);
+        if (tau + delta < bound * bound * (1.f - 1e-6f)) {
+            ok = true;
+            break;
+        }
+    }
+    TopK<K> top;
+    if (ok && fd[K2 - 1] <= tau) ok = false;  // too many near ties for the list
+    if (ok) {
+        const Pos4 yi = pos[q];
+        top.init();
+#pragma unroll
+        for (int u = 0; u < K2; u++)
+            if (fd[u] <= tau && fi[u] >= 0) {
+                const Pos4 yj = pos[fi[u]];
+                top.insert(dist2_exact(yi, yj, p), (int)yj.w, fi[u]);
+            }
+    } else {
+        knn_exact<K>(pos, cell_start, p, q, top);
     }
 #pragma unroll
     for (int t = 0; t < K; t++) {
@@ -430,19 +568,21 @@ int build_knn(DeviceState& d, cudaStream_t s, int* dup_flag_host) {
     p.k = d.k;
     int* flags = (int*)(d.counters + 3);
     SDOT_CUDA_TRY(cudaMemsetAsync(flags, 0, 4, s));
-    unsigned nb = (unsigned)((d.N + 127) / 128);
-    if (d.k <= 8)
-        knn_kernel<8><<<nb, 128, 0, s>>>(d.pos, d.grid.cell_start, p, d.knn, d.knn_d2k, flags);
-    else if (d.k <= 16)
-        knn_kernel<16><<<nb, 128, 0, s>>>(d.pos, d.grid.cell_start, p, d.knn, d.knn_d2k, flags);
-    else if (d.k <= 24)
-        knn_kernel<24><<<nb, 128, 0, s>>>(d.pos, d.grid.cell_start, p, d.knn, d.knn_d2k, flags);
-    else if (d.k <= 32)
-        knn_kernel<32><<<nb, 128, 0, s>>>(d.pos, d.grid.cell_start, p, d.knn, d.knn_d2k, flags);
-    else if (d.k <= 48)
-        knn_kernel<48><<<nb, 128, 0, s>>>(d.pos, d.grid.cell_start, p, d.knn, d.knn_d2k, flags);
-    else
-        knn_kernel<64><<<nb, 128, 0, s>>>(d.pos, d.grid.cell_start, p, d.knn, d.knn_d2k, flags);
+    // FP32 grid-local offsets and grid cells: posf and leafc serve as scratch here (the
+    // first Laguerre evaluation rewrites both)
+    const unsigned nb = (unsigned)((d.N + 127) / 128);
+    knn_prep_kernel<<<nb, 128, 0, s>>>(d.pos, d.N, p, d.posf, d.leafc);
+    note_launch();
+    SDOT_CUDA_TRY(cudaGetLastError());
+#define SDOT_KNN_LAUNCH(KK, F)                                                           \
+    knn_kernel<KK, F><<<nb, 128, 0, s>>>(d.pos, d.posf, d.leafc, d.grid.cell_start, p, \
+                                         d.knn, d.knn_d2k, flags)
+    if (d.k <= 8) SDOT_KNN_LAUNCH(8, true);
+    else if (d.k <= 16) SDOT_KNN_LAUNCH(16, true);
+    else if (d.k <= 24) SDOT_KNN_LAUNCH(24, true);
+    else if (d.k <= 32) SDOT_KNN_LAUNCH(32, false);
+    else SDOT_KNN_LAUNCH(64, false);
+#undef SDOT_KNN_LAUNCH
     note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
     int h = 0;

@@ -192,7 +192,7 @@ int csr_fill(DeviceState& d, cudaStream_t s);                      // col, val, 
 int assemble_csr_user(DeviceState& d, int64_t nnz, cudaStream_t s);
 // sliced-ELL Newton matrix: sell_build counts (sell_ptr in slice widths, *entries the
 // storage it needs), sell_fill writes it (arrays of that capacity) and dinv
-int sell_build(DeviceState& d, int64_t* entries, int mixed, cudaStream_t s);
+int sell_build(DeviceState& d, int64_t* entries, int64_t* offdiag, cudaStream_t s);
 int sell_fill(DeviceState& d, int mixed, cudaStream_t s);
 // Jacobi-preconditioned CG on L x = (nu - V) - mean, until ||r|| <= rtol ||r0||
 int cg_solve(DeviceState& d, double rtol, int maxit, int* iters, double* rel_res,

@@ -403,7 +403,22 @@ __global__ void partial_sum_kernel(const double* __restrict__ part, int nb, int 
     if (threadIdx.x == 0) *out = t;
 }
 
-int sell_build(DeviceState& d, int64_t* entries, int mixed, cudaStream_t s) {
+// the kept off-diagonal entries of all rows (the counts of the slice widths pass)
+__global__ void sell_nnz_kernel(const int32_t* __restrict__ fcnt, const int32_t* __restrict__ fcol,
+                                const double* __restrict__ fval, int64_t N,
+                                unsigned long long* __restrict__ out) {
+    unsigned long long k = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int n = fcnt[i];
+        for (int t = 0; t < n; t++)
+            if (sym_value(fcnt, fcol, fval, i, t) > 0.0) k++;
+    }
+    for (int o = 16; o > 0; o >>= 1) k += __shfl_xor_sync(FULLMASK, k, o);
+    if ((threadIdx.x & 31) == 0 && k) atomicAdd(out, k);
+}
+
+int sell_build(DeviceState& d, int64_t* entries, int64_t* offdiag, cudaStream_t s) {
     const int64_t N = d.N;
     const int64_t nslice = (N + 31) / 32;
     const int nb = 8 * num_sms();
@@ -413,11 +428,17 @@ int sell_build(DeviceState& d, int64_t* entries, int mixed, cudaStream_t s) {
     SDOT_CUDA_TRY(cudaMemsetAsync(d.sell_w + nslice, 0, 4, s));
     int rc = scan_exclusive_i32_to_i64(d.sell_w, d.sell_ptr, nslice + 1, d.partials + 65536, s);
     if (rc) return rc;
-    int64_t tot = 0;
-    SDOT_CUDA_TRY(cudaMemcpyAsync(&tot, d.sell_ptr + nslice, 8, cudaMemcpyDeviceToHost, s));
+    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(d.scal + 40);
+    SDOT_CUDA_TRY(cudaMemsetAsync(cnt, 0, 8, s));
+    sell_nnz_kernel<<<nb, CG_THREADS, 0, s>>>(d.fcnt, d.fcol, d.fval, N, cnt);
+    note_launch();
+    SDOT_CUDA_TRY(cudaGetLastError());
+    int64_t h[2] = {0, 0};
+    SDOT_CUDA_TRY(cudaMemcpyAsync(&h[0], d.sell_ptr + nslice, 8, cudaMemcpyDeviceToHost, s));
+    SDOT_CUDA_TRY(cudaMemcpyAsync(&h[1], cnt, 8, cudaMemcpyDeviceToHost, s));
     SDOT_CUDA_TRY(cudaStreamSynchronize(s));
-    *entries = 32 * tot;  // slice widths sum to tot; each slice holds 32 rows
-    (void)mixed;
+    *entries = 32 * h[0];  // slice widths sum to h[0]; each slice holds 32 rows
+    *offdiag = h[1];
     return SDOT_OK;
 }
 

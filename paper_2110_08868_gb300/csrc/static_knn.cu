@@ -34,7 +34,9 @@ constexpr size_t ST_IPERM = ST_PERM + ST_align(ST_N * 4);
 constexpr size_t ST_KNN = ST_IPERM + ST_align(ST_N * 4);
 constexpr size_t ST_D2K = ST_KNN + ST_align(ST_N * ST_K * 4);
 constexpr size_t ST_START = ST_D2K + ST_align(ST_N * 8);
-constexpr size_t ST_COUNTERS = ST_START + ST_align((ST_N + 1) * 4);
+constexpr size_t ST_OFF = ST_START + ST_align((ST_N + 1) * 4);  // FP32 grid offsets
+constexpr size_t ST_CELLC = ST_OFF + ST_align(ST_N * 16);            // grid cells
+constexpr size_t ST_COUNTERS = ST_CELLC + ST_align(ST_N * 4);
 constexpr size_t ST_TEMP = ST_COUNTERS + 256;
 // build_grid temp: keys (N), counts and fills (ncell each), a flag, then scan temp
 constexpr size_t ST_TEMP_BYTES = ST_align(ST_N * 4) + 2 * ST_align(ST_N * 4) + 256 + 64 * 1024;
@@ -127,6 +129,8 @@ extern "C" int sdot_knn_static(const double* pos, int64_t N, const double box[3]
     d.knn = (int32_t*)(base + ST_KNN);
     d.knn_d2k = (double*)(base + ST_D2K);
     d.grid.cell_start = (int32_t*)(base + ST_START);
+    d.posf = (float4*)(base + ST_OFF);
+    d.leafc = (int32_t*)(base + ST_CELLC);
     d.counters = (int32_t*)(base + ST_COUNTERS);
     // the grid of sdot_create's default (2 seeds per cell) never has more cells than
     // seeds, which the scratch layout assumes

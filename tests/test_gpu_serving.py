@@ -127,3 +127,30 @@ def test_admission_budget_and_failures():
         assert info["finished"] == 4
     finally:
         srv.close()
+
+
+@pytest.mark.parametrize("batch_clip", [True, False])
+def test_server_job_matches_the_oracle(batch_clip):
+    # a 12^3 job solved by the server (in a mix with two other jobs) to 1e-10, against
+    # the oracle's own damped-Newton solve of the same box to 1e-11: the displacements
+    # agree within 1e-6 lattice spacings (eq. laguerrecell at the unique solution)
+    import sdot_oracle as O
+
+    n, seed = 12, 1011
+    y = _box(n, seed)
+    a = 1.0 / n
+    nu = ics.uniform_masses(y.shape[0], 1.0)
+    srv = B.Server(max_active=4, batch_clip=batch_clip)
+    try:
+        others = [srv.submit(_box(m, s), [1.0] * 3, 1e-6) for m, s in ((16, 1012), (14, 1013))]
+        jid = srv.submit(y, [1.0] * 3, 1e-10, precision="fp64")
+        assert srv.wait(jid, 120.0)
+        r = srv.result(jid)
+        for o in others:
+            assert srv.wait(o, 120.0)
+            srv.result(o)
+    finally:
+        srv.close()
+    assert r["stats"]["max_rel_err"] <= 1e-10
+    _, info = O.solve(y, nu, 1.0, tol=1e-11)
+    assert np.max(np.abs(r["disp"] - info["disp"])) <= 1e-6 * a
