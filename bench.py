@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--box-n", type=int, default=0,
+                    help="profiling aid: the workload's recipe at lattice side n (clump "
+                         "counts scaled with n^3); the bench line names the smaller box")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--tol", type=float, default=1e-4)
     ap.add_argument("--no-fp64-compare", action="store_true",
@@ -158,11 +161,20 @@ def max_over_ranks(ms, dist):
     return float(t.item())
 
 
-def replica_config(workload, rank, world):
-    """Replicas only: every rank solves its own box (seed offset by 1000 x rank)."""
+def replica_config(workload, rank, world, box_n=0):
+    """Replicas only: every rank solves its own box (seed offset by 1000 x rank). box_n:
+    the same recipe at lattice side box_n (clump counts scaled with the seed count)."""
     from paper_2110_08868_gb300 import ics
 
     cfg = dict(ics.CONFIGS[workload])
+    if box_n:
+        f = (box_n / cfg["n"]) ** 3
+        cfg["n"] = box_n
+        if cfg.get("clumps"):
+            c = dict(cfg["clumps"])
+            c["n_clumps"] = max(1, int(round(c["n_clumps"] * f)))
+            c["n_extra"] = max(1, int(round(c["n_extra"] * f)))
+            cfg["clumps"] = c
     if world > 1:
         cfg["seed"] = cfg["seed"] + 1000 * rank
     return cfg
@@ -294,7 +306,7 @@ def run_native(args, rank, world, local):
         dist.init_process_group("gloo")
     from paper_2110_08868_gb300 import ics
 
-    y, nu, L = ics.make_config(**replica_config(args.workload, rank, world))
+    y, nu, L = ics.make_config(**replica_config(args.workload, rank, world, args.box_n))
     N = int(y.shape[0])
     box = [L, L, L]
     pos_dev = torch.from_numpy(y).cuda()
@@ -328,7 +340,9 @@ def run_native(args, rank, world, local):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
+        torch.cuda.nvtx.range_push("bench_timed")
         ms_each, info = eval_steps(B, ctx, psis, vol, cen, hcsr, args.steps, stream)
+        torch.cuda.nvtx.range_pop()
         ev1.record(stream)
         torch.cuda.synchronize()
         if dist is not None:
@@ -426,7 +440,8 @@ def run_native(args, rank, world, local):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "N": N, "precision": args.precision,
+            "config": {"workload": args.workload + (f" at n={args.box_n}" if args.box_n else ""),
+                       "N": N, "precision": args.precision,
                        "tol": args.tol, "k": 24,
                        "step": "one sdot_laguerre (volumes, centroids, CSR Hessian) at the "
                                "converged weights of the solve to tol, alternating with its "

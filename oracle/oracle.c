@@ -479,3 +479,138 @@ int oracle_knn(int64_t N, const double* pos, const double* L, int k, int64_t n_o
     }
     return 0;
 }
+
+/*
+ * Kantorovich potential at tau_I on a mesh (Sec. "Monge-Ampere-Kantorovich
+ * Reconstruction", the Legendre transform of psi):
+ *     phi_I(q) = min_i [1/2 |q - x_i|^2 - psi_i]  (minimum image),
+ * attained in the Laguerre cell i(q) that contains q. Evaluated by brute force over all
+ * seeds at the M^3 mesh points q = (m + 1/2) L / M; owner[m] = i(q), the lowest index on
+ * a tie.
+ */
+int oracle_potential_mesh(int64_t N, const double* pos, const double* psi, const double* L,
+                          int M, double* phi, int64_t* owner) {
+    if (M < 1) return -1;
+    const int64_t nm = (int64_t)M * M * M;
+#pragma omp parallel for schedule(static)
+    for (int64_t m = 0; m < nm; m++) {
+        const int64_t mx = m % M, my = (m / M) % M, mz = m / ((int64_t)M * M);
+        const double q[3] = {(mx + 0.5) * L[0] / M, (my + 0.5) * L[1] / M, (mz + 0.5) * L[2] / M};
+        double best = INFINITY;
+        int64_t arg = -1;
+        for (int64_t j = 0; j < N; j++) {
+            double s = 0.0;
+            for (int e = 0; e < 3; e++) {
+                const double d = wrap1(q[e] - pos[3 * j + e], L[e]);
+                s += d * d;
+            }
+            const double f = 0.5 * s - psi[j];
+            if (f < best) {
+                best = f;
+                arg = j;
+            }
+        }
+        phi[m] = best;
+        owner[m] = arg;
+    }
+    return 0;
+}
+
+/*
+ * Zel'dovich move of the cells and their mass density on an Eulerian mesh (Sec.
+ * "Monge-Ampere-Kantorovich Reconstruction", last paragraph; Fig. 1). The point q of
+ * cell V_i moves to q + lambda (x_i - q) (lambda = D(tau)/D(tau_F), 0 <= lambda < 1),
+ * so the cell becomes its image under the homothety of ratio 1 - lambda centred at
+ * x_i and carries the mass m_i spread uniformly over it. The mass of mesh voxel v is
+ *     sum_i m_i |h_i(V_i) cap v| / |h_i(V_i)| = sum_i m_i |V_i cap h_i^-1(v)| / |V_i|,
+ * computed here by clipping each cell with the six planes of h_i^-1(v) for every voxel
+ * its moved bounding box meets. rho[v] = mass / voxel volume (M^3 voxels of side L/M).
+ * Cells are the certified cells of oracle_cells; the sums run serially over cells in
+ * index order.
+ */
+int oracle_deposit(int64_t N, const double* pos, const double* psi, const double* mass,
+                   const double* L, int M, double lambda, double* rho) {
+    if (M < 1 || !(lambda >= 0.0 && lambda < 1.0)) return -1;
+    const int64_t nm = (int64_t)M * M * M;
+    for (int64_t m = 0; m < nm; m++) rho[m] = 0.0;
+    double psi_max = -INFINITY;
+    for (int64_t j = 0; j < N; j++)
+        if (psi[j] > psi_max) psi_max = psi[j];
+    work_t* W = (work_t*)malloc(sizeof(work_t));
+    poly_t* R = (poly_t*)malloc(sizeof(poly_t));
+    W->cand = (cand_t*)malloc(sizeof(cand_t) * (size_t)N);
+    W->ncand_cap = N;
+    int agg = 0;
+    const double s = 1.0 - lambda;
+    const double h[3] = {L[0] / M, L[1] / M, L[2] / M};
+    for (int64_t i = 0; i < N && !(agg & OR_OVERFLOW); i++) {
+        double dpsi = psi_max - psi[i];
+        if (dpsi < 0) dpsi = 0;
+        int st = cell_certified(W, i, N, pos, psi, L, dpsi);
+        if (st == OR_NOT_CERTIFIED) {
+            if (W->ncand_cap < 386 * N) {
+                free(W->cand);
+                W->ncand_cap = 386 * N;
+                W->cand = (cand_t*)malloc(sizeof(cand_t) * (size_t)W->ncand_cap);
+            }
+            st = cell_brute(W, i, N, pos, psi, L, dpsi);
+        }
+        agg |= st;
+        if (st != OR_OK) continue;
+        double vol, m1[3], i2;
+        poly_integrals(&W->P, &vol, m1, &i2);
+        if (!(vol > 0.0)) continue;
+        /* local bounding box (p = q - x_i), its moved image, the voxels it meets */
+        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int f = 0; f < W->P.nf; f++)
+            for (int k = 0; k < W->P.nv[f]; k++)
+                for (int e = 0; e < 3; e++) {
+                    lo[e] = fmin(lo[e], W->P.v[f][k][e]);
+                    hi[e] = fmax(hi[e], W->P.v[f][k][e]);
+                }
+        const double* y = pos + 3 * i;
+        int64_t v0[3], v1[3];
+        for (int e = 0; e < 3; e++) {
+            v0[e] = (int64_t)floor((y[e] + s * lo[e]) / h[e]);
+            v1[e] = (int64_t)floor((y[e] + s * hi[e]) / h[e]);
+        }
+        for (int64_t vz = v0[2]; vz <= v1[2]; vz++)
+            for (int64_t vy = v0[1]; vy <= v1[1]; vy++)
+                for (int64_t vx = v0[0]; vx <= v1[0]; vx++) {
+                    const int64_t vv[3] = {vx, vy, vz};
+                    /* copy the cell, clip it by the voxel pulled back by the homothety */
+                    R->nf = W->P.nf;
+                    for (int f = 0; f < W->P.nf; f++) {
+                        R->nv[f] = W->P.nv[f];
+                        R->tag[f] = W->P.tag[f];
+                        R->dlen[f] = W->P.dlen[f];
+                        memcpy(R->v[f], W->P.v[f], sizeof(double) * 3 * W->P.nv[f]);
+                    }
+                    int empty = 0;
+                    for (int e = 0; e < 3 && !empty; e++) {
+                        const double blo = (vv[e] * h[e] - y[e]) / s;
+                        const double bhi = ((vv[e] + 1) * h[e] - y[e]) / s;
+                        double n[3] = {0, 0, 0};
+                        n[e] = 1.0;
+                        if (poly_clip(R, &W->Q, n, bhi, -2, 1.0, W->cap) < 0) agg |= OR_OVERFLOW;
+                        n[e] = -1.0;
+                        if (R->nf > 0 && poly_clip(R, &W->Q, n, -blo, -2, 1.0, W->cap) < 0)
+                            agg |= OR_OVERFLOW;
+                        if (R->nf == 0) empty = 1;
+                    }
+                    if (empty) continue;
+                    double v2, mm[3], ii;
+                    poly_integrals(R, &v2, mm, &ii);
+                    if (!(v2 > 0.0)) continue;
+                    const int64_t wx = ((vx % M) + M) % M, wy = ((vy % M) + M) % M,
+                                  wz = ((vz % M) + M) % M;
+                    rho[(wz * M + wy) * M + wx] += mass[i] * (v2 / vol);
+                }
+    }
+    free(W->cand);
+    free(W);
+    free(R);
+    const double vox = h[0] * h[1] * h[2];
+    for (int64_t m = 0; m < nm; m++) rho[m] /= vox;
+    return agg & OR_OVERFLOW ? -2 : 0;
+}

@@ -69,6 +69,10 @@ def _load():
         lib.oracle_cells.restype = ctypes.c_int
         lib.oracle_knn.argtypes = [i64, P, P, ctypes.c_int, i64, P, P, P]
         lib.oracle_knn.restype = ctypes.c_int
+        lib.oracle_potential_mesh.argtypes = [i64, P, P, P, ctypes.c_int, P, P]
+        lib.oracle_potential_mesh.restype = ctypes.c_int
+        lib.oracle_deposit.argtypes = [i64, P, P, P, P, ctypes.c_int, ctypes.c_double, P]
+        lib.oracle_deposit.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -258,3 +262,42 @@ def displacement(ev):
     within half a box of the seed.
     """
     return -ev["local_centroid"]
+
+
+def potential_mesh(pos, psi, box, M):
+    """phi_I at the M^3 mesh points (m + 1/2) L / M, and the cell i(q) containing each
+    (the Legendre transform of psi, Sec. "Monge-Ampere-Kantorovich Reconstruction").
+    Returns (phi[M, M, M], owner[M, M, M]) indexed [z, y, x]."""
+    lib = _load()
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    psi = np.ascontiguousarray(psi, dtype=np.float64)
+    L = _box(box)
+    phi = np.empty(M ** 3)
+    owner = np.empty(M ** 3, dtype=np.int64)
+    if lib.oracle_potential_mesh(pos.shape[0], _ptr(pos), _ptr(psi), _ptr(L), M, _ptr(phi),
+                                 _ptr(owner)) != 0:
+        raise ValueError("M must be >= 1")
+    return phi.reshape(M, M, M), owner.reshape(M, M, M)
+
+
+def deposit(pos, psi, box, M, lam, mass=None):
+    """Mass density on the M^3 mesh of the cells moved by the Zel'dovich map
+    q -> q + lam (x_i - q) (each cell shrunk about its point by 1 - lam, its mass spread
+    uniformly), by exact clipping with the voxels (last paragraph of Sec.
+    "Monge-Ampere-Kantorovich Reconstruction", Fig. 1). Indexed [z, y, x]."""
+    lib = _load()
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    psi = np.ascontiguousarray(psi, dtype=np.float64)
+    L = _box(box)
+    N = pos.shape[0]
+    if mass is None:
+        mass = np.full(N, float(np.prod(L)) / N)
+    mass = np.ascontiguousarray(mass, dtype=np.float64)
+    rho = np.empty(M ** 3)
+    rc = lib.oracle_deposit(N, _ptr(pos), _ptr(psi), _ptr(mass), _ptr(L), M, float(lam),
+                            _ptr(rho))
+    if rc == -1:
+        raise ValueError("need M >= 1 and 0 <= lam < 1")
+    if rc == -2:
+        raise RuntimeError("oracle polytope capacity exceeded")
+    return rho.reshape(M, M, M)

@@ -178,6 +178,7 @@ int ensure_csr_capacity(sdot_ctx* c, int64_t nnz) {
 
 // assemble the sorted CSR: count (fixes nnz), grow the arrays if needed, fill
 int build_csr(sdot_ctx* c) {
+    NvtxRange nv("hessian_csr");
     int64_t nnz = 0;
     int rc = csr_count(c->d, &nnz, c->stream);
     if (rc) return rc;
@@ -190,6 +191,7 @@ int build_csr(sdot_ctx* c) {
 // the sliced-ELL Newton matrix: count, grow the arrays if needed (8 bytes of value per
 // entry, enough for either precision), fill
 int build_sell(sdot_ctx* c, int mixed) {
+    NvtxRange nv("newton_matrix");
     int64_t ent = 0, offd = 0;
     int rc = sell_build(c->d, &ent, &offd, c->stream);
     if (rc) return rc;
@@ -293,6 +295,7 @@ namespace sdot {
 // context on a stream of its own)
 int create_context(const double* pos, const double* mass, int64_t N, const double box[3],
                    const sdot_options* opt, cudaStream_t stream, sdot_ctx** out) {
+    NvtxRange nv("sdot_create");
     g_err.clear();
     if (!out) {
         set_error("sdot_create: out is NULL");
@@ -526,6 +529,7 @@ int sdot_create(const double* pos, const double* mass, int64_t N, const double b
 
 int sdot_laguerre(sdot_ctx* c, const double* psi, double* volumes, double* centroids,
                   sdot_csr* hess) {
+    NvtxRange nv("sdot_laguerre");
     g_err.clear();
     if (!c) return SDOT_ERR_ARG;
     DeviceState& d = c->d;
@@ -591,6 +595,7 @@ int sdot_laguerre(sdot_ctx* c, const double* psi, double* volumes, double* centr
 }
 
 int sdot_solve(sdot_ctx* c, double tol, const double* psi0, sdot_stats* st) {
+    NvtxRange nv("sdot_solve");
     g_err.clear();
     if (!c || !(tol > 0)) {
         set_error("sdot_solve: need a context and tol > 0");

@@ -327,6 +327,7 @@ static ClipParams make_clip_params(DeviceState& d, const double* psi) {
 
 int evaluate_cells(DeviceState& d, const double* psi, int precision, EvalResult* res,
                    cudaStream_t s) {
+    NvtxRange nv("laguerre_cells");
     int rc = build_pyramid(d, psi, s);
     if (rc) return rc;
     ClipParams cp = make_clip_params(d, psi);

@@ -557,6 +557,7 @@ __global__ void __launch_bounds__(128) knn_kernel(const Pos4* __restrict__ pos,
 }
 
 int build_knn(DeviceState& d, cudaStream_t s, int* dup_flag_host) {
+    NvtxRange nv("knn");
     KnnParams p;
     for (int a = 0; a < 3; a++) {
         p.G[a] = d.grid.G[a];

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -123,6 +124,15 @@ struct DeviceState {
     double* scal;             // device scalars
     Grid grid;
     Pyramid pyr;
+};
+
+// NVTX range for the lifetime of the object (phases of the hot path, visible to
+// profilers; a no-op when no tool is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
 // ---------------------------------------------------------------------------

@@ -470,6 +470,7 @@ int sell_fill(DeviceState& d, int mixed, cudaStream_t s) {
 
 int cg_solve(DeviceState& d, double rtol, int maxit, int* iters, double* rel_res,
              cudaStream_t s) {
+    NvtxRange nv("cg");
     const int64_t N = d.N;
     const int64_t nslice = (N + 31) / 32;
     // memory-bound loops: 8 blocks of 8 warps per SM keep enough loads in flight for

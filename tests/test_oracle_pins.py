@@ -328,3 +328,86 @@ def test_newton_c1_small_converges():
     assert info["hist"][-1] <= 1e-10
     assert abs(psi.sum()) < 1e-12
     np.testing.assert_allclose(info["vol"], nu, rtol=1e-10)
+
+
+# --- phi_I on a mesh, the Zel'dovich move and the Eulerian deposit ----------------------
+
+def test_potential_lattice_closed_form():
+    # psi = 0 on a lattice: phi_I(q) = 1/2 |q - nearest lattice point|^2
+    n, L, M = 4, 1.0, 8
+    a = L / n
+    phi, owner = O.potential_mesh(ics.lattice(n, L), np.zeros(n ** 3), L, M)
+    g = (np.arange(M) + 0.5) * L / M
+    off = (g - (np.floor(g / a) + 0.5) * a) ** 2  # squared offset per axis
+    expect = 0.5 * (off[:, None, None] + off[None, :, None] + off[None, None, :])
+    np.testing.assert_allclose(phi, expect, rtol=1e-14)
+    c = np.floor(g / a).astype(int)
+    np.testing.assert_array_equal(owner, c[None, None, :] + n * c[None, :, None]
+                                  + n * n * c[:, None, None])
+
+
+def test_potential_plane_wave_closed_form():
+    # separable plane wave: the cells are the lattice cubes, so the owner of q is the
+    # cube containing it and phi_I(q) = 1/2 |q - y_j|^2 - psi_j (no mesh point lies on a
+    # cube face for n = 5, M = 12)
+    n, L, M = 5, 1.0, 12
+    a = L / n
+    y, psi, _ = plane_wave(n, L, [0.03, 0.02, 0.035], [0.3, 1.1, -0.4])
+    phi, owner = O.potential_mesh(y, psi, L, M)
+    g = (np.arange(M) + 0.5) * L / M
+    c = np.floor(g / a).astype(int)
+    j = c[None, None, :] + n * c[None, :, None] + n * n * c[:, None, None]
+    np.testing.assert_array_equal(owner, j)
+    q = np.stack(np.meshgrid(g, g, g, indexing="ij")[::-1], -1)  # [z, y, x, (x, y, z)]
+    d = q - y[j]
+    d -= L * np.round(d / L)
+    np.testing.assert_allclose(phi, 0.5 * (d ** 2).sum(-1) - psi[j], rtol=0, atol=1e-14)
+
+
+def _overlap_1d(c, w, M, L):
+    """fraction of each interval [c_i - w/2, c_i + w/2] (periodic) in each of M bins"""
+    h = L / M
+    out = np.zeros((c.size, M))
+    for i, ci in enumerate(c):
+        lo, hi = ci - 0.5 * w, ci + 0.5 * w
+        for v in range(int(np.floor(lo / h)), int(np.floor(hi / h)) + 1):
+            ov = min(hi, (v + 1) * h) - max(lo, v * h)
+            if ov > 0:
+                out[i, v % M] += ov / w
+    return out
+
+
+@pytest.mark.parametrize("lam,M", [(0.0, 5), (0.3, 9), (0.7, 12)])
+def test_deposit_plane_wave_closed_form(lam, M):
+    # the cells of the separable plane wave are the lattice cubes; moved by the
+    # Zel'dovich map each becomes a cube of side (1 - lam) a centred at q + lam s(q), so
+    # the voxel masses are products of 1-D interval overlaps
+    n, L = 5, 1.0
+    a = L / n
+    amps, phases = [0.03, 0.02, 0.035], [0.3, 1.1, -0.4]
+    y, psi, s = plane_wave(n, L, amps, phases)
+    rho = O.deposit(y, psi, L, M, lam)
+    g = (np.arange(n) + 0.5) * a
+    w = (1 - lam) * a
+    ov = []
+    for ax, (A, ph) in enumerate(zip(amps, phases)):
+        c = g + lam * A * np.sin(2 * np.pi * g / L + ph)
+        ov.append(_overlap_1d(c, w, M, L).sum(axis=0))
+    nu, vox = a ** 3, (L / M) ** 3
+    expect = nu / vox * ov[2][:, None, None] * ov[1][None, :, None] * ov[0][None, None, :]
+    np.testing.assert_allclose(rho, expect, rtol=1e-11, atol=1e-12)
+
+
+def test_deposit_conserves_mass_and_is_uniform_at_the_solution():
+    # any psi: the deposited masses sum to the seeds' masses; at the OT solution and
+    # lam = 0 every cell has volume nu_i, so the density is 1 everywhere
+    n, L, M = 5, 1.0, 7
+    y, _, _ = ics.zeldovich_box(n, L, ics.spectrum_kinv, 0.3, 12)
+    N = y.shape[0]
+    nu = ics.uniform_masses(N, L)
+    psi = 0.05 * (L / n) ** 2 * np.random.default_rng(3).standard_normal(N)
+    for lam in (0.0, 0.4):
+        rho = O.deposit(y, psi, L, M, lam)
+        assert abs(rho.sum() * (L / M) ** 3 - nu.sum()) < 1e-12 * L ** 3
+    psi_s, _ = O.solve(y, nu, L, tol=1e-12)
+    np.testing.assert_allclose(O.deposit(y, psi_s, L, M, 0.0), 1.0, rtol=0, atol=1e-10)
