@@ -235,6 +235,31 @@ int sdot_cell_status(sdot_ctx* ctx, uint8_t* status);
 int sdot_knn_static(const double* pos, int64_t N, const double box[3], int k, int32_t* nbr,
                     void* stream);
 
+/*
+ * After the solve: the Kantorovich potential at tau_I on a mesh and the mass density of
+ * the cells moved to an intermediate time (Sec. "Monge-Ampere-Kantorovich
+ * Reconstruction": the Legendre transform of psi, and the last paragraph; Fig. 1).
+ * At the context's current psi (the cells of its last evaluation at that psi; the
+ * call evaluates the diagram first if needed).
+ *  lambda: D(tau) / D(tau_F) in [0, 1): the Zel'dovich map q -> q + lambda (x_i - q)
+ *          moves every point of cell i towards its point x_i, i.e. shrinks the cell
+ *          about x_i by the factor 1 - lambda; lambda = 0 is tau_I.
+ *  mesh:   M in [1, 2048] points per axis; value m = (z M + y) M + x belongs to the
+ *          voxel [x, x+1] x [y, y+1] x [z, z+1] L/M and to its centre (m + 1/2) L/M.
+ *  rho:    M^3 doubles out (host or device), or NULL: the mass density of the moved
+ *          cells (each carries its mass nu_i uniformly), computed by exact intersection
+ *          of every moved cell with the voxels; mean 1 when sum nu = |box|.
+ *  phi:    M^3 doubles out, or NULL: phi_I(q) = min_i [1/2 |q - x_i|^2 - psi_i]
+ *          (minimum image) at the voxel centres.
+ *  owner:  M^3 int32 out, or NULL: the cell containing each voxel centre (caller
+ *          order; the lowest index when the centre lies on a facet).
+ * The device buffers it needs (16 M^3 bytes, plus staging for host outputs) come from
+ * the context's allocator and are kept for the next call. SDOT_ERR_CAPACITY if a cell
+ * cannot be rebuilt from its facets in the large polytope.
+ */
+int sdot_mesh(sdot_ctx* ctx, double lambda, int mesh, double* rho, double* phi,
+              int32_t* owner);
+
 /* Statistics of the context's last Laguerre evaluation (host memory out). */
 int sdot_last_eval(const sdot_ctx* ctx, sdot_eval_info* info);
 

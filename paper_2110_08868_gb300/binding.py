@@ -95,7 +95,8 @@ class sdot_server_info(ctypes.Structure):
 EXPORTS = ["sdot_default_options", "sdot_create", "sdot_set_stream", "sdot_set_allocator",
            "sdot_laguerre",
            "sdot_solve", "sdot_csr_copy", "sdot_get_psi", "sdot_displacement", "sdot_knn",
-           "sdot_cell_status", "sdot_knn_static", "sdot_last_eval", "sdot_size", "sdot_destroy",
+           "sdot_cell_status", "sdot_knn_static", "sdot_last_eval", "sdot_mesh", "sdot_size",
+           "sdot_destroy",
            "sdot_kernel_launches", "sdot_last_error",
            "sdot_server_default_options", "sdot_server_footprint", "sdot_server_create",
            "sdot_server_submit", "sdot_server_poll", "sdot_server_wait", "sdot_server_result",
@@ -139,6 +140,7 @@ def load(path=LIB_PATH):
     lib.sdot_knn_static.argtypes = [P, I64, P, I, P, P]
     lib.sdot_size.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I)]
     lib.sdot_last_eval.argtypes = [P, ctypes.POINTER(sdot_eval_info)]
+    lib.sdot_mesh.argtypes = [P, D, I, P, P, P]
     lib.sdot_destroy.argtypes = [P]
     lib.sdot_destroy.restype = None
     lib.sdot_kernel_launches.argtypes = []
@@ -292,6 +294,11 @@ def sdot_knn_static(pos, box, k, nbr, stream=None):
                                   int(k), _ptr(nbr, np.int32), ctypes.c_void_p(h) if h else None)
 
 
+def sdot_mesh(ctx, lam, mesh, rho=None, phi=None, owner=None):
+    return load().sdot_mesh(ctx, float(lam), int(mesh), _ptr(rho), _ptr(phi),
+                            _ptr(owner, np.int32))
+
+
 def sdot_last_eval(ctx, info):
     return load().sdot_last_eval(ctx, ctypes.byref(info))
 
@@ -361,6 +368,16 @@ class Solver:
         out = np.empty((self.N, 3))
         check(sdot_displacement(self.ctx, out))
         return out
+
+    def mesh(self, lam, M):
+        """rho (moved-cell mass density), phi (phi_I) and owner on the M^3 mesh, each
+        shaped (M, M, M) and indexed [z, y, x]."""
+        rho = np.empty(M ** 3)
+        phi = np.empty(M ** 3)
+        owner = np.empty(M ** 3, dtype=np.int32)
+        check(sdot_mesh(self.ctx, lam, M, rho, phi, owner))
+        return {"rho": rho.reshape(M, M, M), "phi": phi.reshape(M, M, M),
+                "owner": owner.reshape(M, M, M)}
 
     def status(self):
         out = np.empty(self.N, dtype=np.uint8)

@@ -16,7 +16,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsdot.so")
-SOURCES = ["grid_knn.cu", "clip.cu", "linalg.cu", "api.cu", "static_knn.cu", "serve.cu"]
+SOURCES = ["grid_knn.cu", "clip.cu", "linalg.cu", "api.cu", "static_knn.cu", "serve.cu",
+           "mesh.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

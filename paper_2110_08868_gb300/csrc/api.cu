@@ -45,10 +45,15 @@ struct sdot_ctx {
     int64_t nnz = 0;
     int64_t nnz_cap_u = 0;
     int64_t sell_cap = 0;     // entries the sliced-ELL arrays hold
+    void* mesh_scratch = nullptr;  // sdot_mesh: fixed-point masses and phi bits
+    size_t mesh_scratch_bytes = 0;
+    void* mesh_stage = nullptr;    // sdot_mesh: device copies of host outputs
+    size_t mesh_stage_bytes = 0;
     bool eval_valid = false;  // last evaluation is at d.psi
     float ms_knn = 0;
     EvalResult last{};
     int last_prec = SDOT_PREC_MIXED;  // precision of the last evaluation
+    bool has_eval = false;            // some evaluation has run (c->last is set)
     int64_t sell_entries = 0;         // stored entries of the last Newton matrix
     int64_t sell_offdiag = 0;         // its nonzero off-diagonal entries
     bool dry = false;         // allocation plan only: count bytes, allocate nothing
@@ -140,7 +145,10 @@ int eval_at(sdot_ctx* c, const double* psi_sorted, EvalResult* r, int precision 
     if (rc) return rc;
     c->last = *r;
     c->last_prec = prec;
-    c->eval_valid = true;
+    c->has_eval = true;
+    // the context's diagram is at its current psi only for an evaluation at d.psi (a
+    // line-search trial evaluates psi_trial)
+    c->eval_valid = psi_sorted == c->d.psi;
     return SDOT_OK;
 }
 
@@ -493,12 +501,57 @@ int sdot_set_stream(sdot_ctx* c, void* stream) {
     return SDOT_OK;
 }
 
+int sdot_mesh(sdot_ctx* c, double lambda, int mesh, double* rho, double* phi, int32_t* owner) {
+    g_err.clear();
+    if (!c || mesh < 1 || mesh > 2048 || !(lambda >= 0.0 && lambda < 1.0) ||
+        (!rho && !phi && !owner)) {
+        set_error("sdot_mesh: need a context, 1 <= mesh <= 2048, 0 <= lambda < 1 and an output");
+        return SDOT_ERR_ARG;
+    }
+    DeviceState& d = c->d;
+    cudaStream_t s = c->stream;
+    int rc;
+    if (!c->eval_valid) {
+        EvalResult r;
+        if ((rc = eval_at(c, d.psi, &r))) return rc;
+        if ((rc = eval_status(r, "sdot_mesh"))) return rc;
+    }
+    const int64_t n = (int64_t)mesh * mesh * mesh;
+    auto grow = [&](void** p, size_t* have, size_t need) -> int {
+        if (need <= *have) return SDOT_OK;
+        dev_free(c, *p);
+        *p = nullptr;
+        *have = 0;
+        int r = dev_alloc(c, p, need);
+        if (r) return r;
+        *have = need;
+        return SDOT_OK;
+    };
+    if ((rc = grow(&c->mesh_scratch, &c->mesh_scratch_bytes, (size_t)n * 16))) return rc;
+    const bool rho_dev = !rho || is_device_ptr(rho), phi_dev = !phi || is_device_ptr(phi),
+               own_dev = !owner || is_device_ptr(owner);
+    const size_t stage = (rho_dev ? 0 : 8) + (phi_dev ? 0 : 8) + (own_dev ? 0 : 4);
+    if (stage && (rc = grow(&c->mesh_stage, &c->mesh_stage_bytes, (size_t)n * stage))) return rc;
+    char* sp = (char*)c->mesh_stage;
+    double* rho_d = rho_dev ? rho : (double*)sp;
+    if (!rho_dev) sp += (size_t)n * 8;
+    double* phi_d = phi_dev ? phi : (double*)sp;
+    if (!phi_dev) sp += (size_t)n * 8;
+    int32_t* own_d = own_dev ? owner : (int32_t*)sp;
+    if ((rc = mesh_eval(d, mesh, lambda, rho_d, phi_d, own_d, c->mesh_scratch, s))) return rc;
+    if (!rho_dev) SDOT_CUDA_TRY(cudaMemcpyAsync(rho, rho_d, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+    if (!phi_dev) SDOT_CUDA_TRY(cudaMemcpyAsync(phi, phi_d, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+    if (!own_dev) SDOT_CUDA_TRY(cudaMemcpyAsync(owner, own_d, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+    SDOT_CUDA_TRY(cudaStreamSynchronize(s));
+    return SDOT_OK;
+}
+
 int sdot_last_eval(const sdot_ctx* c, sdot_eval_info* info) {
     if (!c || !info) {
         set_error("sdot_last_eval: need a context and info");
         return SDOT_ERR_ARG;
     }
-    if (!c->eval_valid) {
+    if (!c->has_eval) {
         set_error("sdot_last_eval: the context has not been evaluated yet");
         return SDOT_ERR_ARG;
     }

@@ -139,6 +139,7 @@ struct ClipParams {
     uint32_t* topo;                  // N * TOPO stored vertices (three plane indices)
     uint8_t* topo_n;                 // N stored vertex counts (0: none)
     float nsz[MAXLEV][3];            // node size per pyramid level, units of a
+    int pass;                        // 1 security test, 2 re-queue, 3 FP64 re-clip
 };
 
 __device__ __forceinline__ double wrapd(double dx, double L, double halfL) {
@@ -1087,6 +1088,36 @@ __device__ __noinline__ bool integrate(Poly<R, C>& P, const ClipParams& cp, cons
     // surface closure check and the facet areas in R
     double vol6 = 0, mx = 0, my = 0, mz = 0;
     R sx = 0, sy = 0, sz = 0, sabs = 0;
+    // FP32 consistency check (degenerate facets): two facet planes that meet at a vertex
+    // while their normals are less than ANGLE_MIN apart (the bisectors of seeds packed in
+    // a clump, seen from a cell a few spacings away) meet in an edge whose FP32 position
+    // is off by about (plane rounding) / angle, far above the cell's own rounding; such a
+    // cell fails the check and is clipped again in FP64. Box planes take no part.
+    if (sizeof(R) == 4) {
+        constexpr float SIN2_MIN = 0.03f * 0.03f;  // ANGLE_MIN = 0.03 rad
+        bool ill = false;
+        for (int s2 = lane; s2 < P.nt; s2 += 32) {
+            const uint32_t t = P.tri[s2];
+            const uint32_t ia = t & 0xff, ib = (t >> 8) & 0xff, ic = (t >> 16) & 0xff;
+            const V4<R> A = P.pl[ia], Bq = P.pl[ib], Cq = P.pl[ic];
+            const float la2 = A.x * A.x + A.y * A.y + A.z * A.z;
+            const float lb2 = Bq.x * Bq.x + Bq.y * Bq.y + Bq.z * Bq.z;
+            const float lc2 = Cq.x * Cq.x + Cq.y * Cq.y + Cq.z * Cq.z;
+            const float bcx = Bq.y * Cq.z - Bq.z * Cq.y, bcy = Bq.z * Cq.x - Bq.x * Cq.z,
+                        bcz = Bq.x * Cq.y - Bq.y * Cq.x;
+            const float cax = Cq.y * A.z - Cq.z * A.y, cay = Cq.z * A.x - Cq.x * A.z,
+                        caz = Cq.x * A.y - Cq.y * A.x;
+            const float abx = A.y * Bq.z - A.z * Bq.y, aby = A.z * Bq.x - A.x * Bq.z,
+                        abz = A.x * Bq.y - A.y * Bq.x;
+            if (ia >= 6 && ib >= 6 && abx * abx + aby * aby + abz * abz < SIN2_MIN * la2 * lb2)
+                ill = true;
+            if (ib >= 6 && ic >= 6 && bcx * bcx + bcy * bcy + bcz * bcz < SIN2_MIN * lb2 * lc2)
+                ill = true;
+            if (ic >= 6 && ia >= 6 && cax * cax + cay * cay + caz * caz < SIN2_MIN * lc2 * la2)
+                ill = true;
+        }
+        if (__any_sync(FULLMASK, ill)) bad = true;
+    }
     constexpr int FPL = (C::MP + 31) / 32;  // faces handled per lane
     // apex of the tetrahedron fans: the centre o of the vertices' bounding box, so the
     // determinants involve offsets of the cell's own size even when the cell lies far
@@ -1556,13 +1587,13 @@ __device__ __forceinline__ void process_cell(Poly<R, C>& P, const ClipParams& cp
         // pass was re-queued (8); a cell of the FP64 re-clip keeps what sent it there
         // (4: FP32 check failed, 32/64/128: small capacity exceeded) and its re-queue
         uint32_t hist = 0;
-        if (MODE == MODE_FULL && !BIG) hist = CS_UNCERTIFIED;
-        if (BIG)
+        if (cp.pass == 2) hist = CS_UNCERTIFIED;
+        if (cp.pass == 3)
             hist = cp.status[i] & (CS_INCONSISTENT | CS_UNCERTIFIED | CS_CAP_POLY | CS_CAP_FACE |
                                    CS_CAP_STACK);
         cp.status[i] = (uint8_t)(st | hist);
         // FP32 cells failing a check, and cells over the small capacity, are clipped
-        // again in FP64 with the large capacity
+        // again in FP64 (small polytope first, the large one for its overflows)
         const bool redo = !BIG && (((sizeof(R) == 4) && (st & CS_INCONSISTENT)) ||
                                    (st & CS_CAPACITY));
         if (redo) {
@@ -1570,6 +1601,148 @@ __device__ __forceinline__ void process_cell(Poly<R, C>& P, const ClipParams& cp
             cp.q64_out[q] = (int32_t)i;
         }
     }
+}
+
+}  // namespace sdot
+
+namespace sdot {
+
+// Volume of the polytope (units of a^3), FP64 sum of per-face fan tetrahedra from the
+// centre of the vertices' bounding box, the faces found as in integrate. Every lane
+// gets the value; 0 when a face cycle is broken.
+template <typename R, class C>
+__device__ __noinline__ double poly_volume(Poly<R, C>& P, int lane) {
+    constexpr int FPL = (C::MP + 31) / 32;
+    R o[3];
+    {
+        R mn[3] = {R(1e30), R(1e30), R(1e30)}, mxv[3] = {R(-1e30), R(-1e30), R(-1e30)};
+        for (int s2 = lane; s2 < P.nt; s2 += 32) {
+            const R v[3] = {P.vx[s2], P.vy[s2], P.vz[s2]};
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                mn[a] = fmin(mn[a], v[a]);
+                mxv[a] = fmax(mxv[a], v[a]);
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            for (int q = 16; q > 0; q >>= 1) {
+                mn[a] = fmin(mn[a], __shfl_xor_sync(FULLMASK, mn[a], q));
+                mxv[a] = fmax(mxv[a], __shfl_xor_sync(FULLMASK, mxv[a], q));
+            }
+            o[a] = R(0.5) * (mn[a] + mxv[a]);
+        }
+    }
+    const int nt = P.nt, np = P.np;
+    for (int f = lane; f < np; f += 32) P.fend[f] = 0u;
+    __syncwarp();
+    for (int s2 = lane; s2 < nt; s2 += 32) {
+        const uint32_t t = P.tri[s2];
+        atomicAdd(&P.fend[t & 0xff], 1u);
+        atomicAdd(&P.fend[(t >> 8) & 0xff], 1u);
+        atomicAdd(&P.fend[(t >> 16) & 0xff], 1u);
+    }
+    __syncwarp();
+    int fcount[FPL];
+    {
+        uint32_t carry = 0;
+        for (int k = 0; k < FPL; k++) {
+            const int f = lane + 32 * k;
+            const uint32_t c = f < np ? P.fend[f] : 0u;
+            fcount[k] = (int)c;
+            uint32_t incl = c;
+            for (int q = 1; q < 32; q <<= 1) {
+                const uint32_t y = __shfl_up_sync(FULLMASK, incl, q);
+                if (lane >= q) incl += y;
+            }
+            if (f < np) P.fend[f] = carry + incl - c;
+            carry += __shfl_sync(FULLMASK, incl, 31);
+        }
+    }
+    __syncwarp();
+    for (int s2 = lane; s2 < nt; s2 += 32) {
+        const uint32_t t = P.tri[s2];
+        const uint32_t a = t & 0xff, b = (t >> 8) & 0xff, c = (t >> 16) & 0xff;
+        const uint32_t sv = (uint32_t)s2 << 16;
+        P.fent[atomicAdd(&P.fend[a], 1u)] = b | (c << 8) | sv;
+        P.fent[atomicAdd(&P.fend[b], 1u)] = c | (a << 8) | sv;
+        P.fent[atomicAdd(&P.fend[c], 1u)] = a | (b << 8) | sv;
+    }
+    __syncwarp();
+    double vol6 = 0.0;
+    bool ok = true;
+    for (int k = 0; k < FPL; k++) {
+        const int f = lane + 32 * k;
+        const int m = fcount[k];
+        if (f >= np || m == 0) continue;
+        if (m < 3) {
+            ok = false;
+            continue;
+        }
+        const int e0 = (int)P.fend[f] - m;
+        int first = e0;
+        for (int e = e0 + 1; e < e0 + m; e++)
+            if ((P.fent[e] >> 16) < (P.fent[first] >> 16)) first = e;
+        uint32_t ecur = P.fent[first];
+        const uint32_t x0 = ecur & 0xff;
+        V3<R> v0 = vert(P, ecur >> 16);
+        v0.x -= o[0];
+        v0.y -= o[1];
+        v0.z -= o[2];
+        V3<R> vp = v0;
+        R fv6 = 0;
+        for (int step = 1; step < m; step++) {
+            const uint32_t yv = (ecur >> 8) & 0xff;
+            int nxt = -1;
+            for (int e = e0; e < e0 + m; e++)
+                if ((P.fent[e] & 0xff) == yv) {
+                    nxt = e;
+                    break;
+                }
+            if (nxt < 0 || nxt == first) {
+                ok = false;
+                break;
+            }
+            ecur = P.fent[nxt];
+            V3<R> vc = vert(P, ecur >> 16);
+            vc.x -= o[0];
+            vc.y -= o[1];
+            vc.z -= o[2];
+            if (step >= 2) {
+                const R ax = vp.x - v0.x, ay = vp.y - v0.y, az = vp.z - v0.z;
+                const R bx = vc.x - v0.x, by = vc.y - v0.y, bz = vc.z - v0.z;
+                const R cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;
+                fv6 += v0.x * cx + v0.y * cy + v0.z * cz;
+            }
+            vp = vc;
+        }
+        if (((ecur >> 8) & 0xff) != x0) ok = false;
+        vol6 += (double)fv6;
+    }
+    vol6 = warp_sum(vol6);
+    ok = __all_sync(FULLMASK, ok);
+    return ok ? vol6 / 6.0 : 0.0;
+}
+
+// P2 <- P1 (warp-uniform)
+template <typename R, class C>
+__device__ __noinline__ void poly_copy(Poly<R, C>& P2, const Poly<R, C>& P1, int lane) {
+    for (int q = lane; q < P1.np; q += 32) {
+        P2.pl[q] = P1.pl[q];
+        P2.plen[q] = P1.plen[q];
+        P2.pj[q] = P1.pj[q];
+    }
+    for (int s = lane; s < P1.nt; s += 32) {
+        P2.tri[s] = P1.tri[s];
+        P2.vx[s] = P1.vx[s];
+        P2.vy[s] = P1.vy[s];
+        P2.vz[s] = P1.vz[s];
+    }
+    if (lane == 0) {
+        P2.np = P1.np;
+        P2.nt = P1.nt;
+    }
+    __syncwarp();
 }
 
 }  // namespace sdot

@@ -322,8 +322,13 @@ static ClipParams make_clip_params(DeviceState& d, const double* psi) {
     cp.work_counter = nullptr;
     cp.worklist = nullptr;
     cp.nwork = d.N;
+    cp.pass = 1;
     return cp;
 }
+
+// the cells of context d at its current psi, for rebuilding them from their facets in
+// FP64 (mesh.cu)
+ClipParams mesh_clip_params(DeviceState& d) { return make_clip_params(d, d.psi); }
 
 int evaluate_cells(DeviceState& d, const double* psi, int precision, EvalResult* res,
                    cudaStream_t s) {
@@ -345,6 +350,7 @@ int evaluate_cells(DeviceState& d, const double* psi, int precision, EvalResult*
     cp.work_counter = d.counters + 2;
     cp.worklist = nullptr;
     cp.nwork = d.N;
+    cp.pass = 1;
     rc = precision == SDOT_PREC_FP64 ? launch_clip<double, CapS, MODE_CERTIFY>(cp, s)
                                      : launch_clip<float, CapS, MODE_CERTIFY>(cp, s);
     if (rc) return rc;
@@ -358,6 +364,7 @@ int evaluate_cells(DeviceState& d, const double* psi, int precision, EvalResult*
         cp.work_counter = d.counters + 4;
         cp.worklist = d.queue;
         cp.nwork = requeued;
+        cp.pass = 2;
         rc = precision == SDOT_PREC_FP64 ? launch_clip<double, CapS, MODE_FULL>(cp, s)
                                          : launch_clip<float, CapS, MODE_FULL>(cp, s);
         if (rc) return rc;
@@ -366,14 +373,23 @@ int evaluate_cells(DeviceState& d, const double* psi, int precision, EvalResult*
     }
     cudaEventRecord(ep2, s);
     int64_t reclipped = cnt[1];
-    // pass 3: FP64 re-clip with the large capacity (cells failing the FP32 checks,
-    // cells over the small capacity)
+    // pass 3: FP64 re-clip of the cells failing the FP32 checks or over the small
+    // capacity: the small polytope first (its overflows are appended to the same queue),
+    // then the large one for those
     if (reclipped > 0) {
+        cp.pass = 3;
         cp.work_counter = d.counters + 5;
         cp.worklist = d.queue64;
         cp.nwork = reclipped;
-        rc = launch_clip<double, CapL, MODE_FULL>(cp, s);
-        if (rc) return rc;
+        if (precision != SDOT_PREC_FP64) {
+            if ((rc = launch_clip<double, CapS, MODE_FULL>(cp, s))) return rc;
+            SDOT_CUDA_TRY(cudaMemcpyAsync(cnt, d.counters, 8, cudaMemcpyDeviceToHost, s));
+            SDOT_CUDA_TRY(cudaStreamSynchronize(s));
+            cp.work_counter = d.counters + 6;
+            cp.worklist = d.queue64 + reclipped;
+            cp.nwork = (int64_t)cnt[1] - reclipped;
+        }
+        if (cp.nwork > 0 && (rc = launch_clip<double, CapL, MODE_FULL>(cp, s))) return rc;
     }
     cudaEventRecord(e1, s);
     cell_reduce_kernel<<<RED_BLOCKS, 256, 0, s>>>(d.vol, d.nu, d.status, d.N, d.partials);
@@ -577,6 +593,7 @@ int evaluate_cells_batch(DeviceState* const* ds, const double* const* psis, cons
     // pass 1: every cell of every job
     for (int j = 0; j < n; j++) {
         cps[j].worklist = nullptr;
+        cps[j].pass = 1;
         nwork[j] = ds[j]->N;
     }
     if ((rc = launch_table<float, CapS, MODE_CERTIFY>(cps, nwork, is32, 0, sc, s)) ||
@@ -594,6 +611,7 @@ int evaluate_cells_batch(DeviceState* const* ds, const double* const* psis, cons
     for (int j = 0; j < n; j++) {
         requeued[j] = sc->cnt_host[2 * j];
         cps[j].worklist = ds[j]->queue;
+        cps[j].pass = 2;
         nwork[j] = requeued[j];
         any = any || requeued[j] > 0;
     }
@@ -614,6 +632,7 @@ int evaluate_cells_batch(DeviceState* const* ds, const double* const* psis, cons
     for (int j = 0; j < n; j++) {
         reclipped[j] = sc->cnt_host[2 * j + 1];
         cps[j].worklist = ds[j]->queue64;
+        cps[j].pass = 3;
         nwork[j] = reclipped[j];
         any = any || nwork[j] > 0;
     }

@@ -196,6 +196,11 @@ int evaluate_cells_batch(DeviceState* const* ds, const double* const* psis, cons
 typedef int (*EvalHook)(void* user, DeviceState* d, const double* psi, int precision,
                         EvalResult* res, cudaStream_t s);
 
+// mesh.cu: phi_I and owners at the M^3 mesh points and the mass density of the cells
+// moved by lambda (any output may be null); scratch holds 16 M^3 bytes
+int mesh_eval(DeviceState& d, int M, double lambda, double* rho_dev, double* phi_dev,
+              int32_t* owner_dev, void* scratch, cudaStream_t s);
+
 // linalg.cu
 int csr_count(DeviceState& d, int64_t* nnz_out, cudaStream_t s);  // row_ptr and nnz
 int csr_fill(DeviceState& d, cudaStream_t s);                      // col, val, dinv
