@@ -43,9 +43,12 @@ FLOP_PER_CELL = 6000.0
 FP32_LANES_PER_SM = 128
 N_SM = 152
 # CG vector traffic per row and iteration: the update kernel reads u, p, w, s, x, r and
-# the inverse diagonal and writes p, s, x, r, u (96 B); the SpMV reads u_i and writes w_i
-# (16 B); the gathered neighbour values u_j are counted once per row (8 B)
-CG_BYTES_PER_ROW = 120
+# the inverse diagonal and writes p, s, x, r, u and the FP32 copy of u (100 B); the SpMV
+# reads u_i in FP64 and FP32 and writes w_i (20 B); the gathered FP32 neighbour values
+# u_j are counted once per row (4 B)
+CG_BYTES_PER_ROW = 124
+# per off-diagonal entry of L: int32 column + FP32 weight
+CG_BYTES_PER_ENTRY = 8
 # DRAM bytes per launch from an ncu capture of the current kernels (None: not captured
 # since the kernel last changed)
 CLIP_TRAFFIC = None
@@ -394,13 +397,13 @@ def run_native(args, rank, world, local):
                 "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {clock_ghz:.3f} "
                                "GHz (median SM clock sampled under load)",
                 "per_launch_ms": pass1_ms, "flop_per_cell": FLOP_PER_CELL}
-    # CG (HBM-bound): algorithmic bytes per iteration = the stored sliced-ELL entries
-    # (int32 column + weight) + the vectors (see CG_BYTES_PER_ROW)
+    # CG (HBM-bound): algorithmic bytes per iteration = the off-diagonal entries of L
+    # (int32 column + FP32 weight; the sliced-ELL padding is not counted) + the vectors
+    # (see CG_BYTES_PER_ROW)
     cg = None
     if solve_st["cg_iters"] > 0:
         it_ms = solve_st["ms_cg"] / solve_st["cg_iters"]
-        wbytes = 4 if args.precision == "mixed" else 8
-        bytes_it = solve_st["hess_slots"] * (4 + wbytes) + CG_BYTES_PER_ROW * N
+        bytes_it = solve_st["hess_offdiag"] * CG_BYTES_PER_ENTRY + CG_BYTES_PER_ROW * N
         gbs = bytes_it / (it_ms / 1e3) / 1e9
         hbm = peaks.get("hbm_gbs", 6786.2)
         cg = {"kernel": "CG iteration (cg_spmv_kernel + cg_update_kernel)", "bound": "hbm",

@@ -196,9 +196,8 @@ int build_csr(sdot_ctx* c) {
     return SDOT_OK;
 }
 
-// the sliced-ELL Newton matrix: count, grow the arrays if needed (8 bytes of value per
-// entry, enough for either precision), fill
-int build_sell(sdot_ctx* c, int mixed) {
+// the sliced-ELL Newton matrix: count, grow the arrays if needed, fill
+int build_sell(sdot_ctx* c) {
     NvtxRange nv("newton_matrix");
     int64_t ent = 0, offd = 0;
     int rc = sell_build(c->d, &ent, &offd, c->stream);
@@ -212,10 +211,10 @@ int build_sell(sdot_ctx* c, int mixed) {
         c->d.sell_val = nullptr;
         const int64_t cap = ent + ent / 4 + 1024;
         if ((rc = alloc_n(c, &c->d.sell_col, cap))) return rc;
-        if ((rc = dev_alloc(c, &c->d.sell_val, (size_t)cap * 8))) return rc;
+        if ((rc = alloc_n(c, &c->d.sell_val, cap))) return rc;
         c->sell_cap = cap;
     }
-    return sell_fill(c->d, mixed, c->stream);
+    return sell_fill(c->d, c->stream);
 }
 
 // Every device array of a context for d.N seeds in box d.L (the hash grid, kNN lists,
@@ -251,7 +250,7 @@ int alloc_context(sdot_ctx* c) {
         (rc = alloc_n(c, &d.counters, 32)) || (rc = alloc_n(c, &d.row_ptr, N + 1)) ||
         (rc = alloc_n(c, &d.rowcnt, N + 1)) || (rc = alloc_n(c, &d.x, N)) ||
         (rc = alloc_n(c, &d.r, N)) || (rc = alloc_n(c, &d.z, N)) || (rc = alloc_n(c, &d.p, N)) ||
-        (rc = alloc_n(c, &d.q, N)) || (rc = alloc_n(c, &d.sv, N)) ||
+        (rc = alloc_n(c, &d.q, N)) || (rc = alloc_n(c, &d.sv, N)) || (rc = alloc_n(c, &d.uf, N)) ||
         (rc = alloc_n(c, &d.dinv, N)) || (rc = alloc_n(c, &d.sell_ptr, (N + 31) / 32 + 1)) ||
         (rc = alloc_n(c, &d.sell_w, (N + 31) / 32 + 1)) ||
         (rc = alloc_n(c, &d.partials, 1 << 20)) || (rc = alloc_n(c, &d.scal, 64)) ||
@@ -716,7 +715,7 @@ int sdot_solve(sdot_ctx* c, double tol, const double* psi0, sdot_stats* st) {
             rc = SDOT_ERR_MAXIT;
             break;
         }
-        if ((rc = build_sell(c, c->opt.precision == SDOT_PREC_MIXED))) break;
+        if ((rc = build_sell(c))) break;
         int cg_it = 0;
         double cg_res = 0;
         cudaEventRecord(c0, s);

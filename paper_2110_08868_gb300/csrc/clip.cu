@@ -28,7 +28,7 @@ constexpr int clip_min_blocks() {
 
 template <typename R, class C, int MODE>
 __global__ void __launch_bounds__(WARPS_PER_BLOCK_CLIP * 32, (clip_min_blocks<R, C>()))
-    clip_kernel(ClipParams cp) {
+    clip_kernel(const __grid_constant__ ClipParams cp) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Poly<R, C>* polys = reinterpret_cast<Poly<R, C>*>(smem_raw);
     const int lane = threadIdx.x & 31;
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK_CLIP * 32, (clip_min_blocks<R,
             if (bt.start[mid] <= w) lo = mid;
             else hi = mid - 1;
         }
-        const ClipParams cp = bt.jobs[lo];
+        const ClipParams& cp = bt.jobs[lo];
         const float psimax_glob = top_psimax(cp, lane);
         const float halfLmin = 0.5f * fminf(cp.Lt[0], fminf(cp.Lt[1], cp.Lt[2]));
         process_cell<R, C, MODE>(P, cp, (int64_t)(w - bt.start[lo]), psimax_glob, halfLmin,

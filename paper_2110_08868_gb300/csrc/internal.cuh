@@ -112,14 +112,14 @@ struct DeviceState {
     double* val_u;
     // CG vectors (x: the Newton direction, z: u = M^-1 r, q: w = L u, sv: s = L p)
     double *x, *r, *z, *p, *q, *sv, *dinv;
+    float* uf;                // u rounded to FP32, the operand the SpMV gathers
     // the Newton matrix L in sliced-ELL form (slices of 32 rows, entry k of row
-    // 32 l + m at sell_ptr[l] + 32 k + m): neighbour column and weight A/|d| (FP32 in
-    // mixed precision, else FP64); the diagonal is implied (zero row sums)
+    // 32 l + m at sell_ptr[l] + 32 k + m, columns ascending within a row): neighbour
+    // column and FP32 weight A/|d|; the diagonal is implied (zero row sums)
     int64_t* sell_ptr;        // nslice + 1
     int32_t* sell_w;          // nslice + 1 slice widths (scan input)
     int32_t* sell_col;
-    void* sell_val;
-    int sell_mixed;
+    float* sell_val;
     double* partials;         // reduction partials
     double* scal;             // device scalars
     Grid grid;
@@ -208,7 +208,7 @@ int assemble_csr_user(DeviceState& d, int64_t nnz, cudaStream_t s);
 // sliced-ELL Newton matrix: sell_build counts (sell_ptr in slice widths, *entries the
 // storage it needs), sell_fill writes it (arrays of that capacity) and dinv
 int sell_build(DeviceState& d, int64_t* entries, int64_t* offdiag, cudaStream_t s);
-int sell_fill(DeviceState& d, int mixed, cudaStream_t s);
+int sell_fill(DeviceState& d, cudaStream_t s);
 // Jacobi-preconditioned CG on L x = (nu - V) - mean, until ||r|| <= rtol ||r0||
 int cg_solve(DeviceState& d, double rtol, int maxit, int* iters, double* rel_res,
              cudaStream_t s);

@@ -185,12 +185,13 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 
 // Off-diagonal entries kept per row (symmetrised facets of positive weight); one warp
-// per slice of 32 rows, whose width (longest row) it records.
+// per slice of 32 rows, whose width (longest row) it records, and the total count.
 __global__ void sell_count_kernel(const int32_t* __restrict__ fcnt, const int32_t* __restrict__ fcol,
                                   const double* __restrict__ fval, int64_t N, int64_t nslice,
-                                  int32_t* __restrict__ width) {
+                                  int32_t* __restrict__ width, unsigned long long* __restrict__ nnz) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    unsigned long long tot = 0;
     for (int64_t sl = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); sl < nslice;
          sl += nw) {
         const int64_t i = sl * 32 + lane;
@@ -202,18 +203,20 @@ __global__ void sell_count_kernel(const int32_t* __restrict__ fcnt, const int32_
         }
         const int w = __reduce_max_sync(FULLMASK, kept);
         if (lane == 0) width[sl] = w;
+        tot += (unsigned long long)__reduce_add_sync(FULLMASK, (unsigned)kept);
     }
+    if (lane == 0 && tot) atomicAdd(nnz, tot);
 }
 
 // The entries of each slice column by column (entry k of row 32 sl + l at
-// ptr[sl] + 32 k + l), padded with zero weights on the row's own column; the
-// Jacobi inverse diagonal from the stored (rounded) weights, so the stored matrix has
-// exactly zero row sums.
-template <typename T>
+// ptr[sl] + 32 k + l), each row in increasing column order, padded with zero weights
+// on the row's own column. Weights are stored in FP32 in both precisions (the SpMV
+// works in FP32 per entry); the Jacobi inverse diagonal is taken from the stored
+// weights, so the stored matrix has exactly zero row sums.
 __global__ void sell_fill_kernel(const int32_t* __restrict__ fcnt, const int32_t* __restrict__ fcol,
                                  const double* __restrict__ fval, int64_t N, int64_t nslice,
                                  const int64_t* __restrict__ ptr, int32_t* __restrict__ col,
-                                 T* __restrict__ val, double* __restrict__ dinv) {
+                                 float* __restrict__ val, double* __restrict__ dinv) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t sl = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); sl < nslice;
@@ -228,9 +231,19 @@ __global__ void sell_fill_kernel(const int32_t* __restrict__ fcnt, const int32_t
             for (int t = 0; t < n && k < w; t++) {
                 const double v = sym_value(fcnt, fcol, fval, i, t);
                 if (!(v > 0.0)) continue;
-                const T vt = (T)v;
-                col[base + 32 * (int64_t)k] = fcol[i * FCAP + t];
-                val[base + 32 * (int64_t)k] = vt;
+                const float vt = (float)v;
+                const int32_t c = fcol[i * FCAP + t];
+                // insertion by column: entry k of neighbouring rows then lies near the
+                // same stencil direction, so the gathers of a warp share cache lines
+                int b = k;
+                for (; b > 0; b--) {
+                    const int32_t cb = col[base + 32 * (int64_t)(b - 1)];
+                    if (cb <= c) break;
+                    col[base + 32 * (int64_t)b] = cb;
+                    val[base + 32 * (int64_t)b] = val[base + 32 * (int64_t)(b - 1)];
+                }
+                col[base + 32 * (int64_t)b] = c;
+                val[base + 32 * (int64_t)b] = vt;
                 diag += (double)vt;
                 k++;
             }
@@ -239,7 +252,7 @@ __global__ void sell_fill_kernel(const int32_t* __restrict__ fcnt, const int32_t
         const int32_t self = i < N ? (int32_t)i : 0;
         for (; k < w; k++) {
             col[base + 32 * (int64_t)k] = self;
-            val[base + 32 * (int64_t)k] = (T)0;
+            val[base + 32 * (int64_t)k] = 0.f;
         }
     }
 }
@@ -256,9 +269,9 @@ __global__ void sell_fill_kernel(const int32_t* __restrict__ fcnt, const int32_t
 __global__ void cg_init_kernel(const double* __restrict__ nu, const double* __restrict__ vol,
                                double mean, const double* __restrict__ dinv, int64_t N,
                                double* __restrict__ x, double* __restrict__ r,
-                               double* __restrict__ u, double* __restrict__ p,
-                               double* __restrict__ sv, double* __restrict__ part,
-                               double* __restrict__ cg) {
+                               double* __restrict__ u, float* __restrict__ uf,
+                               double* __restrict__ p, double* __restrict__ sv,
+                               double* __restrict__ part, double* __restrict__ cg) {
     __shared__ double sh[32];
     double g = 0, rr = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
@@ -268,6 +281,7 @@ __global__ void cg_init_kernel(const double* __restrict__ nu, const double* __re
         x[i] = 0.0;
         r[i] = ri;
         u[i] = ui;
+        uf[i] = (float)ui;
         p[i] = 0.0;
         sv[i] = 0.0;
         g += ri * ui;
@@ -282,13 +296,18 @@ __global__ void cg_init_kernel(const double* __restrict__ nu, const double* __re
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(CG_THREADS)
+// w = L u in the Laplacian form (L u)_i = sum_j c_ij (u_i - u_j). Every stored entry
+// costs two FP32 operations on the FP32 copy of u: GB300 issues FP64 at about two
+// operations per clock per SM, so FP64 arithmetic per entry, not HBM, bounded this
+// loop. A row's sum is rounded to FP64 once. The error of w is that of FP32 products
+// (about 1e-7 of sum_j c_ij (|u_i| + |u_j|)), far below the relative residual the
+// Newton direction is solved to, and the stored matrix keeps its exact zero row sums.
+__global__ void __launch_bounds__(CG_THREADS, 8)
     cg_spmv_kernel(const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
-                   const T* __restrict__ val, int64_t N, int64_t nslice,
-                   const double* __restrict__ u, double* __restrict__ w,
-                   double* __restrict__ part, unsigned int* __restrict__ done,
-                   double* __restrict__ cg) {
+                   const float* __restrict__ val, int64_t N, int64_t nslice,
+                   const float* __restrict__ uf, const double* __restrict__ u,
+                   double* __restrict__ w, double* __restrict__ part,
+                   unsigned int* __restrict__ done, double* __restrict__ cg) {
     __shared__ double sh[32];
     __shared__ bool last;
     const int lane = threadIdx.x & 31;
@@ -299,30 +318,35 @@ __global__ void __launch_bounds__(CG_THREADS)
         const int64_t i = sl * 32 + lane;
         const int64_t b0 = ptr[sl];
         const int wd = (int)((ptr[sl + 1] - b0) >> 5);
-        const double ui = i < N ? u[i] : 0.0;
-        double acc = 0.0;
+        const float ui = i < N ? uf[i] : 0.f;
+        float acc = 0.f;
         const int32_t* cp = col + b0 + lane;
-        const T* vp = val + b0 + lane;
+        const float* vp = val + b0 + lane;
         int k = 0;
-        for (; k + 4 <= wd; k += 4) {
-            const int32_t j0 = cp[0], j1 = cp[32], j2 = cp[64], j3 = cp[96];
-            const T c0 = vp[0], c1 = vp[32], c2 = vp[64], c3 = vp[96];
-            const double u0 = u[j0], u1 = u[j1], u2 = u[j2], u3 = u[j3];
-            acc += (double)c0 * (ui - u0);
-            acc += (double)c1 * (ui - u1);
-            acc += (double)c2 * (ui - u2);
-            acc += (double)c3 * (ui - u3);
-            cp += 128;
-            vp += 128;
+        for (; k + 8 <= wd; k += 8) {
+            int32_t j[8];
+            float c[8], v[8];
+#pragma unroll
+            for (int e = 0; e < 8; e++) {
+                j[e] = cp[32 * e];
+                c[e] = vp[32 * e];
+            }
+#pragma unroll
+            for (int e = 0; e < 8; e++) v[e] = uf[j[e]];
+#pragma unroll
+            for (int e = 0; e < 8; e++) acc = fmaf(c[e], ui - v[e], acc);
+            cp += 256;
+            vp += 256;
         }
         for (; k < wd; k++) {
-            acc += (double)vp[0] * (ui - u[cp[0]]);
+            acc = fmaf(vp[0], ui - uf[cp[0]], acc);
             cp += 32;
             vp += 32;
         }
         if (i < N) {
-            w[i] = acc;
-            dl += acc * ui;
+            const double wi = (double)acc;
+            w[i] = wi;
+            dl += wi * u[i];
         }
     }
     const double a = block_sum(dl, sh);
@@ -368,7 +392,7 @@ __global__ void cg_update_kernel(const double* __restrict__ cg, const double* __
                                  int64_t N, const double* __restrict__ w, double* __restrict__ p,
                                  double* __restrict__ sv, double* __restrict__ x,
                                  double* __restrict__ r, double* __restrict__ u,
-                                 double* __restrict__ part) {
+                                 float* __restrict__ uf, double* __restrict__ part) {
     __shared__ double sh[32];
     const double alpha = __ldcg(&cg[0]), beta = __ldcg(&cg[1]);
     double g = 0, rr = 0;
@@ -383,6 +407,7 @@ __global__ void cg_update_kernel(const double* __restrict__ cg, const double* __
         x[i] += alpha * pi;
         r[i] = ri;
         u[i] = ui;
+        uf[i] = (float)ui;
         g += ri * ui;
         rr += ri * ri;
     }
@@ -403,36 +428,18 @@ __global__ void partial_sum_kernel(const double* __restrict__ part, int nb, int 
     if (threadIdx.x == 0) *out = t;
 }
 
-// the kept off-diagonal entries of all rows (the counts of the slice widths pass)
-__global__ void sell_nnz_kernel(const int32_t* __restrict__ fcnt, const int32_t* __restrict__ fcol,
-                                const double* __restrict__ fval, int64_t N,
-                                unsigned long long* __restrict__ out) {
-    unsigned long long k = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int n = fcnt[i];
-        for (int t = 0; t < n; t++)
-            if (sym_value(fcnt, fcol, fval, i, t) > 0.0) k++;
-    }
-    for (int o = 16; o > 0; o >>= 1) k += __shfl_xor_sync(FULLMASK, k, o);
-    if ((threadIdx.x & 31) == 0 && k) atomicAdd(out, k);
-}
-
 int sell_build(DeviceState& d, int64_t* entries, int64_t* offdiag, cudaStream_t s) {
     const int64_t N = d.N;
     const int64_t nslice = (N + 31) / 32;
     const int nb = 8 * num_sms();
-    sell_count_kernel<<<nb, CG_THREADS, 0, s>>>(d.fcnt, d.fcol, d.fval, N, nslice, d.sell_w);
+    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(d.scal + 40);
+    SDOT_CUDA_TRY(cudaMemsetAsync(cnt, 0, 8, s));
+    sell_count_kernel<<<nb, CG_THREADS, 0, s>>>(d.fcnt, d.fcol, d.fval, N, nslice, d.sell_w, cnt);
     note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
     SDOT_CUDA_TRY(cudaMemsetAsync(d.sell_w + nslice, 0, 4, s));
     int rc = scan_exclusive_i32_to_i64(d.sell_w, d.sell_ptr, nslice + 1, d.partials + 65536, s);
     if (rc) return rc;
-    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(d.scal + 40);
-    SDOT_CUDA_TRY(cudaMemsetAsync(cnt, 0, 8, s));
-    sell_nnz_kernel<<<nb, CG_THREADS, 0, s>>>(d.fcnt, d.fcol, d.fval, N, cnt);
-    note_launch();
-    SDOT_CUDA_TRY(cudaGetLastError());
     int64_t h[2] = {0, 0};
     SDOT_CUDA_TRY(cudaMemcpyAsync(&h[0], d.sell_ptr + nslice, 8, cudaMemcpyDeviceToHost, s));
     SDOT_CUDA_TRY(cudaMemcpyAsync(&h[1], cnt, 8, cudaMemcpyDeviceToHost, s));
@@ -447,25 +454,37 @@ __global__ void scale_ptr_kernel(int64_t* __restrict__ ptr, int64_t n) {
     if (t < n) ptr[t] *= 32;
 }
 
-int sell_fill(DeviceState& d, int mixed, cudaStream_t s) {
+int sell_fill(DeviceState& d, cudaStream_t s) {
     const int64_t N = d.N;
     const int64_t nslice = (N + 31) / 32;
     const int nb = 8 * num_sms();
     scale_ptr_kernel<<<(unsigned)((nslice + 1 + 255) / 256), 256, 0, s>>>(d.sell_ptr, nslice + 1);
     note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
-    if (mixed)
-        sell_fill_kernel<float><<<nb, CG_THREADS, 0, s>>>(d.fcnt, d.fcol, d.fval, N, nslice,
-                                                          d.sell_ptr, d.sell_col,
-                                                          (float*)d.sell_val, d.dinv);
-    else
-        sell_fill_kernel<double><<<nb, CG_THREADS, 0, s>>>(d.fcnt, d.fcol, d.fval, N, nslice,
-                                                           d.sell_ptr, d.sell_col,
-                                                           (double*)d.sell_val, d.dinv);
+    sell_fill_kernel<<<nb, CG_THREADS, 0, s>>>(d.fcnt, d.fcol, d.fval, N, nslice, d.sell_ptr,
+                                               d.sell_col, d.sell_val, d.dinv);
     note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
-    d.sell_mixed = mixed;
     return SDOT_OK;
+}
+
+// Blocks per SM that the CG kernels can all keep resident at once. The SpMV and the
+// update share the per-block partials, so they run on one grid, and that grid is a
+// single wave: a second, partial wave would run its share of the rows at a fraction
+// of the occupancy.
+static int cg_blocks_per_sm() {
+    static int cached = 0;
+    if (cached) return cached;
+    int b = 8, o = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, cg_spmv_kernel, CG_THREADS, 0) ==
+            cudaSuccess && o > 0)
+        b = o < b ? o : b;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, cg_update_kernel, CG_THREADS, 0) ==
+            cudaSuccess && o > 0)
+        b = o < b ? o : b;
+    cudaGetLastError();
+    cached = b;
+    return b;
 }
 
 int cg_solve(DeviceState& d, double rtol, int maxit, int* iters, double* rel_res,
@@ -473,9 +492,8 @@ int cg_solve(DeviceState& d, double rtol, int maxit, int* iters, double* rel_res
     NvtxRange nv("cg");
     const int64_t N = d.N;
     const int64_t nslice = (N + 31) / 32;
-    // memory-bound loops: 8 blocks of 8 warps per SM keep enough loads in flight for
-    // the gathers of the SpMV
-    const int nb = 8 * num_sms();
+    // memory-bound loops, one resident wave of 256-thread blocks
+    const int nb = cg_blocks_per_sm() * num_sms();
     double* part = d.partials;  // 3 per block
     double* cg = d.scal + 16;   // scalars (see cg_spmv_kernel)
     unsigned int* done = reinterpret_cast<unsigned int*>(d.scal + 32);
@@ -488,8 +506,8 @@ int cg_solve(DeviceState& d, double rtol, int maxit, int* iters, double* rel_res
     const double box = d.L[0] * d.L[1] * d.L[2];
     const double mean = (box - sums[0]) / (double)N;
     SDOT_CUDA_TRY(cudaMemsetAsync(done, 0, sizeof(unsigned int), s));
-    cg_init_kernel<<<nb, CG_THREADS, 0, s>>>(d.nu, d.vol, mean, d.dinv, N, d.x, d.r, d.z, d.p,
-                                             d.sv, part, cg);
+    cg_init_kernel<<<nb, CG_THREADS, 0, s>>>(d.nu, d.vol, mean, d.dinv, N, d.x, d.r, d.z, d.uf,
+                                             d.p, d.sv, part, cg);
     note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
     partial_sum_kernel<<<1, CG_THREADS, 0, s>>>(part, nb, 3, 2, hs);
@@ -508,17 +526,11 @@ int cg_solve(DeviceState& d, double rtol, int maxit, int* iters, double* rel_res
     // u lives in d.z and w in d.q
     while (it < maxit) {
         for (int c = 0; c < check && it < maxit; c++, it++) {
-            if (d.sell_mixed)
-                cg_spmv_kernel<float><<<nb, CG_THREADS, 0, s>>>(
-                    d.sell_ptr, d.sell_col, (const float*)d.sell_val, N, nslice, d.z, d.q, part,
-                    done, cg);
-            else
-                cg_spmv_kernel<double><<<nb, CG_THREADS, 0, s>>>(
-                    d.sell_ptr, d.sell_col, (const double*)d.sell_val, N, nslice, d.z, d.q, part,
-                    done, cg);
+            cg_spmv_kernel<<<nb, CG_THREADS, 0, s>>>(d.sell_ptr, d.sell_col, d.sell_val, N, nslice,
+                                                     d.uf, d.z, d.q, part, done, cg);
             note_launch();
             cg_update_kernel<<<nb, CG_THREADS, 0, s>>>(cg, d.dinv, N, d.q, d.p, d.sv, d.x, d.r,
-                                                       d.z, part);
+                                                       d.z, d.uf, part);
             note_launch();
         }
         SDOT_CUDA_TRY(cudaGetLastError());

@@ -65,7 +65,7 @@ using MeshCap = CapL;
 constexpr int MESH_WARPS = 2;
 
 __global__ void __launch_bounds__(MESH_WARPS * 32)
-    mesh_kernel(ClipParams cp, MeshParams mp) {
+    mesh_kernel(const __grid_constant__ ClipParams cp, const __grid_constant__ MeshParams mp) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using PolyT = Poly<double, MeshCap>;
     PolyT* polys = reinterpret_cast<PolyT*>(smem_raw);
