@@ -78,6 +78,7 @@ struct Poly {
             uint32_t fend[C::MP];       // per face: end of its entries in fent
             uint32_t fent[3 * C::MT];   // (x | y << 8 | vertex slot << 16) by face
             uint8_t fmap[C::MP];        // plane slot -> index in the stored topology
+            R fa[C::MP];                // per face: facet coefficient A / |n|, or -1
         };
     };
     float sup[27];            // support max_v v.u over the 26 stencil directions u
@@ -230,8 +231,10 @@ __device__ void poly_init(Poly<R, C>& P, const ClipParams& cp, const float* z, i
     __syncwarp();
 }
 
+// The vertex of planes (a, b, c) of t; well: the triple is well conditioned,
+// det(n_a, n_b, n_c) > dtol |n_a| |n_b| |n_c|.
 template <typename R, class C>
-__device__ __forceinline__ V3<R> vertex_of(const Poly<R, C>& P, uint32_t t, R& det_rel) {
+__device__ __forceinline__ V3<R> vertex_of(const Poly<R, C>& P, uint32_t t, R dtol, bool& well) {
     const V4<R> A = P.pl[t & 0xff], B = P.pl[(t >> 8) & 0xff], Cc = P.pl[(t >> 16) & 0xff];
     // n_b x n_c, n_c x n_a, n_a x n_b
     R bcx = B.y * Cc.z - B.z * Cc.y, bcy = B.z * Cc.x - B.x * Cc.z, bcz = B.x * Cc.y - B.y * Cc.x;
@@ -244,7 +247,7 @@ __device__ __forceinline__ V3<R> vertex_of(const Poly<R, C>& P, uint32_t t, R& d
     v.y = (A.w * bcy + B.w * cay + Cc.w * aby) * inv;
     v.z = (A.w * bcz + B.w * caz + Cc.w * abz) * inv;
     R la = P.plen[t & 0xff], lb = P.plen[(t >> 8) & 0xff], lc = P.plen[(t >> 16) & 0xff];
-    det_rel = det / (la * lb * lc);
+    well = det > dtol * (la * lb * lc);
     return v;
 }
 
@@ -441,9 +444,9 @@ __device__ __noinline__ int poly_clip(Poly<R, C>& P, const V4<R>& pn, R plen, in
                 if (!(bits >> k & 1u)) continue;
                 const uint32_t x = (t >> (8 * k)) & 0xff, y = (t >> (8 * ((k + 1) % 3))) & 0xff;
                 const uint32_t nt3 = pack3(x, y, ps);
-                R det_rel;
-                V3<R> v = vertex_of(P, nt3, det_rel);
-                if (!(det_rel > dtol)) {
+                bool well;
+                V3<R> v = vertex_of(P, nt3, dtol, well);
+                if (!well) {
                     int sk = -1;
                     for (int q = 0; q < nt; q++) {
                         const bool o = (m[q >> 5] >> (q & 31)) & 1u;
@@ -573,8 +576,10 @@ __device__ __forceinline__ Frame make_frame(const ClipParams& cp, const float* z
         float za = zwant[a];
         if (!isfinite(za)) za = 0.f;
         za = fminf(fmaxf(za, -cp.halfLt[a]), cp.halfLt[a]);
+        // snapped to a multiple of q = ht / 4096 (the nearest one up to FP32 rounding of
+        // the quotient; any multiple serves, the choice is deterministic)
         const double q = (double)cp.ht[a] * (1.0 / 4096.0);
-        f.zd[a] = (double)llrint((double)za / q) * q;
+        f.zd[a] = (double)llrintf(za * (4096.f / cp.ht[a])) * q;
         f.z[a] = (float)f.zd[a];
     }
     return f;
@@ -689,90 +694,70 @@ __device__ __forceinline__ float ord2f(uint32_t u) {
     return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
 }
 
-// Support of the polytope (seed-relative coordinates) in the 26 directions u with
-// components in {-1, 0, 1}: sup[(ux + 1) + 3 (uy + 1) + 9 (uz + 1)] = max_v v.u.
-template <typename R, class C>
-__device__ __forceinline__ void poly_support(const Poly<R, C>& P, const Bounds& b, int lane) {
-    Poly<R, C>& Pm = const_cast<Poly<R, C>&>(P);
-    float mx[13], mn[13];
-#pragma unroll
-    for (int k = 0; k < 13; k++) {
-        mx[k] = -1e30f;
-        mn[k] = 1e30f;
-    }
-    for (int s = lane; s < P.nt; s += 32) {
-        const float x = (float)P.vx[s] + b.zf[0], y = (float)P.vy[s] + b.zf[1],
-                    z = (float)P.vz[s] + b.zf[2];
-        // the 13 directions with a positive leading component, (ux, uy, uz)
-        const float d[13] = {x, y, z, x + y, x - y, x + z, x - z, y + z, y - z,
-                             x + y + z, x + y - z, x - y + z, x - y - z};
-#pragma unroll
-        for (int k = 0; k < 13; k++) {
-            mx[k] = fmaxf(mx[k], d[k]);
-            mn[k] = fminf(mn[k], d[k]);
-        }
-    }
-    // direction codes of the 13 (and their negatives, support -min)
-    const int8_t ux[13] = {1, 0, 0, 1, 1, 1, 1, 0, 0, 1, 1, 1, 1};
-    const int8_t uy[13] = {0, 1, 0, 1, -1, 0, 0, 1, 1, 1, 1, -1, -1};
-    const int8_t uz[13] = {0, 0, 1, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1};
-#pragma unroll
-    for (int k = 0; k < 13; k++) {
-        const float hp = ord2f(__reduce_max_sync(FULLMASK, f2ord(mx[k])));
-        const float hn = -ord2f(__reduce_min_sync(FULLMASK, f2ord(mn[k])));
-        if (lane == 0) {
-            Pm.sup[(ux[k] + 1) + 3 * (uy[k] + 1) + 9 * (uz[k] + 1)] = hp;
-            Pm.sup[(1 - ux[k]) + 3 * (1 - uy[k]) + 9 * (1 - uz[k])] = hn;
-        }
-    }
-    __syncwarp();
+// x wrapped into [0, Lt) as fmodf then one period added to a negative remainder would
+// give it. The polytope's centre lies within half a box of its seed, so x is in
+// (-Lt, 2 Lt), where one subtraction (exact, Sterbenz) or addition does it; any other
+// x takes the general path, kept out of line.
+static __device__ __noinline__ float wrap_box_slow(float x, float Lt) {
+    x = fmodf(x, Lt);
+    if (x < 0.f) x += Lt;
+    return x >= Lt ? 0.f : x;
+}
+__device__ __forceinline__ float wrap_box(float x, float Lt) {
+    if (x >= Lt && x < 2.f * Lt) x -= Lt;
+    else if (x < 0.f && x > -Lt) x += Lt;
+    else if (!(x >= 0.f && x < Lt)) return wrap_box_slow(x, Lt);
+    return x >= Lt ? 0.f : x;
 }
 
+// Bounds of the polytope (seed-relative coordinates): its support in the 26 directions
+// u with components in {-1, 0, 1}, sup[(ux + 1) + 3 (uy + 1) + 9 (uz + 1)] = max_v v.u,
+// the bounding box (the supports in the axis directions, exact), the largest |v|^2 (Mv),
+// and the ball around the box centre c holding every vertex (Rc). Lane k < 27 owns
+// direction k (lane 13, the zero direction, takes |v|^2) and scans every vertex from
+// shared memory: one loop, no reductions for the 26 directions.
 template <typename R, class C>
 __device__ __noinline__ void poly_bounds(const Poly<R, C>& P, const ClipParams& cp, Bounds& b,
                                          int lane) {
-    float mn[3] = {1e30f, 1e30f, 1e30f}, mx[3] = {-1e30f, -1e30f, -1e30f};
-    float m2 = 0.f;
-    for (int s = lane; s < P.nt; s += 32) {
-        const float vv[3] = {(float)P.vx[s] + b.zf[0], (float)P.vy[s] + b.zf[1],
-                             (float)P.vz[s] + b.zf[2]};
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            mn[a] = fminf(mn[a], vv[a]);
-            mx[a] = fmaxf(mx[a], vv[a]);
-        }
-        m2 = fmaxf(m2, vv[0] * vv[0] + vv[1] * vv[1] + vv[2] * vv[2]);
+    Poly<R, C>& Pm = const_cast<Poly<R, C>&>(P);
+    const float ux = (float)(lane % 3 - 1), uy = (float)((lane / 3) % 3 - 1),
+                uz = (float)(lane / 9 - 1);
+    const float w2 = lane == 13 ? 1.f : 0.f;
+    const float z0 = b.zf[0], z1 = b.zf[1], z2 = b.zf[2];
+    const int nt = P.nt;
+    float h = lane == 13 ? 0.f : -1e30f;
+#pragma unroll 1
+    for (int s = 0; s < nt; s++) {
+        const float x = (float)P.vx[s] + z0, y = (float)P.vy[s] + z1, z = (float)P.vz[s] + z2;
+        const float d = fmaf(ux, x, fmaf(uy, y, uz * z));
+        h = fmaxf(h, fmaf(w2, fmaf(x, x, fmaf(y, y, z * z)), d));
     }
+    if (lane < 27) Pm.sup[lane] = h;
+    __syncwarp();
+    // +x 14, -x 12, +y 16, -y 10, +z 22, -z 4
+    const int ip[3] = {14, 16, 22}, in[3] = {12, 10, 4};
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        for (int o = 16; o > 0; o >>= 1) {
-            mn[a] = fminf(mn[a], __shfl_xor_sync(FULLMASK, mn[a], o));
-            mx[a] = fmaxf(mx[a], __shfl_xor_sync(FULLMASK, mx[a], o));
-        }
-        b.bmin[a] = mn[a];
-        b.bmax[a] = mx[a];
-        b.c[a] = 0.5f * (mn[a] + mx[a]);
+        b.bmax[a] = P.sup[ip[a]];
+        b.bmin[a] = -P.sup[in[a]];
+        b.c[a] = 0.5f * (b.bmin[a] + b.bmax[a]);
     }
-    m2 = warp_max(m2);
-    b.Mv = 0.5f * m2 * 1.0001f + 1e-6f;
-    poly_support(P, b, lane);
+    b.Mv = 0.5f * P.sup[13] * 1.0001f + 1e-6f;
+    __syncwarp();
+    if (lane == 0) Pm.sup[13] = 0.f;  // the zero direction (never used by the prefilter)
     float r2 = 0.f;
-    for (int s = lane; s < P.nt; s += 32) {
-        const float dx = ((float)P.vx[s] + b.zf[0]) - b.c[0];
-        const float dy = ((float)P.vy[s] + b.zf[1]) - b.c[1];
-        const float dz = ((float)P.vz[s] + b.zf[2]) - b.c[2];
+#pragma unroll 1
+    for (int s = lane; s < nt; s += 32) {
+        const float dx = ((float)P.vx[s] + z0) - b.c[0];
+        const float dy = ((float)P.vy[s] + z1) - b.c[1];
+        const float dz = ((float)P.vz[s] + z2) - b.c[2];
         r2 = fmaxf(r2, dx * dx + dy * dy + dz * dz);
     }
     r2 = warp_max(r2);
     b.Rc = sqrtf(r2) * 1.0001f + 1e-5f;
 #pragma unroll
-    for (int a = 0; a < 3; a++) {
-        float za = b.yabs[a] + b.c[a];
-        za = fmodf(za, cp.Lt[a]);
-        if (za < 0.f) za += cp.Lt[a];
-        if (za >= cp.Lt[a]) za = 0.f;
-        b.cabs[a] = za;
-    }
+    for (int a = 0; a < 3; a++) b.cabs[a] = wrap_box(b.yabs[a] + b.c[a], cp.Lt[a]);
+    __syncwarp();
 }
 
 // distance from p to the interval [lo, lo + w] on a circle of length Lt
@@ -784,28 +769,46 @@ __device__ __forceinline__ float circ_gap(float p, float lo, float w, float Lt) 
     return fminf(t - w, Lt - t);
 }
 
-// True when no seed of node (level l, coordinates X, Y, Z) can cut the polytope:
+// True when no seed of node (X, Y, Z) of a pyramid level can cut the polytope:
 // 1/2 (u - Rc)_+^2 >= Mv + psimax - psi_i with u the distance from the ball centre
-// to the node's box (see the head of this file).
-__device__ __forceinline__ bool node_pruned(const ClipParams& cp, const Bounds& b, int l, int X,
-                                            int Y, int Z) {
-    const float pm =
-        cp.pyr.psimax[cp.pyr.off[l] + (int64_t)((Z * cp.pyr.dim[l][1] + Y) * cp.pyr.dim[l][0] + X)];
+// to the node's box (see the head of this file). The level (its psimax row pmax, node
+// counts d and node size sz) and the ball (centre c in absolute coordinates, Rc, Mv,
+// psi_i) come in registers: the walk loads them once, not per node.
+struct WalkBall {
+    float c[3];
+    float Rc, Mv, psi_i;
+};
+
+__device__ __forceinline__ WalkBall walk_ball(const Bounds& b) {
+    WalkBall w;
+    w.c[0] = b.cabs[0];
+    w.c[1] = b.cabs[1];
+    w.c[2] = b.cabs[2];
+    w.Rc = b.Rc;
+    w.Mv = b.Mv;
+    w.psi_i = b.psi_i;
+    return w;
+}
+
+__device__ __forceinline__ bool node_pruned(const float* __restrict__ pmax, const int d[3],
+                                            const float sz[3], const float Lt[3],
+                                            const WalkBall& wb, int X, int Y, int Z) {
+    const float pm = pmax[(int64_t)((Z * d[1] + Y) * d[0] + X)];
     if (pm == -INFINITY) return true;  // no seed inside
     const int c[3] = {X, Y, Z};
     float u2 = 0.f;
 #pragma unroll
     for (int a = 0; a < 3; a++) {
         // the last node of an axis ends at the box edge
-        const float lo = (float)c[a] * cp.nsz[l][a];
-        const float w = (c[a] + 1 == cp.pyr.dim[l][a]) ? cp.Lt[a] - lo : cp.nsz[l][a];
-        const float g = circ_gap(b.cabs[a], lo, w, cp.Lt[a]);
+        const float lo = (float)c[a] * sz[a];
+        const float w = (c[a] + 1 == d[a]) ? Lt[a] - lo : sz[a];
+        const float g = circ_gap(wb.c[a], lo, w, Lt[a]);
         u2 += g * g;
     }
-    const float du = fmaxf(sqrtf(u2) * (1.f - 1e-6f) - b.Rc, 0.f);
+    const float du = fmaxf(sqrtf(u2) * (1.f - 1e-6f) - wb.Rc, 0.f);
     const float lhs = 0.5f * du * du;
-    const float rhs = b.Mv + (pm - b.psi_i);
-    const float margin = 2e-5f * (lhs + b.Mv + fabsf(pm) + fabsf(b.psi_i)) + 1e-5f;
+    const float rhs = wb.Mv + (pm - wb.psi_i);
+    const float margin = 2e-5f * (lhs + wb.Mv + fabsf(pm) + fabsf(wb.psi_i)) + 1e-5f;
     return lhs - rhs > margin;
 }
 
@@ -1037,6 +1040,8 @@ __device__ __noinline__ bool traverse(Poly<R, C>& P, const ClipParams& cp, const
                                       Bounds& b, int lane, bool& bad, uint32_t& st) {
     if (lane == 0) P.stack[0] = pack_node(cp.pyr.nlev, 0, 0, 0);
     int sp = 1;
+    const float Lt[3] = {cp.Lt[0], cp.Lt[1], cp.Lt[2]};
+    WalkBall wb = walk_ball(b);
     __syncwarp();
     while (sp > 0) {
         const uint32_t e = P.stack[sp - 1];
@@ -1045,15 +1050,18 @@ __device__ __noinline__ bool traverse(Poly<R, C>& P, const ClipParams& cp, const
         const int cl = (int)(e >> 27) - 1;  // level of the children
         const int x0 = 4 * (int)(e & 511u), y0 = 4 * (int)((e >> 9) & 511u),
                   z0 = 4 * (int)((e >> 18) & 511u);
-        const int cdx = cp.pyr.dim[cl][0], cdy = cp.pyr.dim[cl][1], cdz = cp.pyr.dim[cl][2];
+        const int cd[3] = {cp.pyr.dim[cl][0], cp.pyr.dim[cl][1], cp.pyr.dim[cl][2]};
+        const float csz[3] = {cp.nsz[cl][0], cp.nsz[cl][1], cp.nsz[cl][2]};
+        const float* pmax = cp.pyr.psimax + cp.pyr.off[cl];
         // rounds of 32 children; a round is skipped when none of its children exists
-        const int nzr = min(4, cdz - z0);  // child layers along z (2 per round)
+        const int nzr = min(4, cd[2] - z0);  // child layers along z (2 per round)
         WCOUNT(P, 7, 1);
         for (int base = 0; base < 16 * nzr; base += 32) {
             const int t = base + lane;
             const int cx = x0 + (t & 3), cy = y0 + ((t >> 2) & 3), cz = z0 + (t >> 4);
             bool surv = false;
-            if (cx < cdx && cy < cdy && cz < cdz) surv = !node_pruned(cp, b, cl, cx, cy, cz);
+            if (cx < cd[0] && cy < cd[1] && cz < cd[2])
+                surv = !node_pruned(pmax, cd, csz, Lt, wb, cx, cy, cz);
             WCOUNT(P, 2, 32);
             const uint32_t sm = __ballot_sync(FULLMASK, surv);
             if (sm == 0) continue;
@@ -1072,6 +1080,7 @@ __device__ __noinline__ bool traverse(Poly<R, C>& P, const ClipParams& cp, const
             const int64_t leaf = surv ? ((int64_t)cz * cp.G[1] + cy) * cp.G[0] + cx : -1;
             if (process_leaves<R, C, MODE>(P, cp, cc, b, leaf, lane, bad, st) == LEAF_STOP)
                 return false;
+            if (MODE == MODE_FULL) wb = walk_ball(b);  // a clip may have shrunk the polytope
         }
     }
     return true;
@@ -1096,6 +1105,7 @@ __device__ __noinline__ bool integrate(Poly<R, C>& P, const ClipParams& cp, cons
     if (sizeof(R) == 4) {
         constexpr float SIN2_MIN = 0.03f * 0.03f;  // ANGLE_MIN = 0.03 rad
         bool ill = false;
+#pragma unroll 1
         for (int s2 = lane; s2 < P.nt; s2 += 32) {
             const uint32_t t = P.tri[s2];
             const uint32_t ia = t & 0xff, ib = (t >> 8) & 0xff, ic = (t >> 16) & 0xff;
@@ -1118,13 +1128,13 @@ __device__ __noinline__ bool integrate(Poly<R, C>& P, const ClipParams& cp, cons
         }
         if (__any_sync(FULLMASK, ill)) bad = true;
     }
-    constexpr int FPL = (C::MP + 31) / 32;  // faces handled per lane
     // apex of the tetrahedron fans: the centre o of the vertices' bounding box, so the
     // determinants involve offsets of the cell's own size even when the cell lies far
     // from its seed (no cancellation of large terms in FP32)
     R o[3];
     {
         R mn[3] = {R(1e30), R(1e30), R(1e30)}, mxv[3] = {R(-1e30), R(-1e30), R(-1e30)};
+#pragma unroll 1
         for (int s2 = lane; s2 < P.nt; s2 += 32) {
             const R v[3] = {P.vx[s2], P.vy[s2], P.vz[s2]};
 #pragma unroll
@@ -1142,18 +1152,17 @@ __device__ __noinline__ bool integrate(Poly<R, C>& P, const ClipParams& cp, cons
             o[a] = R(0.5) * (mn[a] + mxv[a]);
         }
     }
-    int nf = 0;
-    int32_t fj[FPL];
-    double fc[FPL];
-    int fslot[FPL];
     const int nt = P.nt;
     const int np = P.np;
     // bucket the vertices by face: vertex s = (a, b, c) lies on faces a, b and c, and
     // on face a the cycle continues from it along (b, c). Counts, an exclusive scan
     // over the faces, then the entries (their order inside a face is immaterial: the
-    // walk below starts at the entry of the lowest vertex slot)
+    // walk below starts at the entry of the lowest vertex slot). After the fill,
+    // fend[f] is the end of face f's entries and the start of face f + 1's.
+#pragma unroll 1
     for (int f = lane; f < np; f += 32) P.fend[f] = 0u;
     __syncwarp();
+#pragma unroll 1
     for (int s2 = lane; s2 < nt; s2 += 32) {
         const uint32_t t = P.tri[s2];
         atomicAdd(&P.fend[t & 0xff], 1u);
@@ -1161,24 +1170,23 @@ __device__ __noinline__ bool integrate(Poly<R, C>& P, const ClipParams& cp, cons
         atomicAdd(&P.fend[(t >> 16) & 0xff], 1u);
     }
     __syncwarp();
-    int fcount[FPL];
     {
         uint32_t carry = 0;
-#pragma unroll
-        for (int k = 0; k < FPL; k++) {
-            const int f = lane + 32 * k;
+#pragma unroll 1
+        for (int f0 = 0; f0 < np; f0 += 32) {
+            const int f = f0 + lane;
             const uint32_t c = f < np ? P.fend[f] : 0u;
-            fcount[k] = (int)c;
             uint32_t incl = c;
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(FULLMASK, incl, o);
-                if (lane >= o) incl += y;
+            for (int q = 1; q < 32; q <<= 1) {
+                const uint32_t y = __shfl_up_sync(FULLMASK, incl, q);
+                if (lane >= q) incl += y;
             }
             if (f < np) P.fend[f] = carry + incl - c;  // start, advanced by the fill
             carry += __shfl_sync(FULLMASK, incl, 31);
         }
     }
     __syncwarp();
+#pragma unroll 1
     for (int s2 = lane; s2 < nt; s2 += 32) {
         const uint32_t t = P.tri[s2];
         const uint32_t a = t & 0xff, b = (t >> 8) & 0xff, c = (t >> 16) & 0xff;
@@ -1188,17 +1196,17 @@ __device__ __noinline__ bool integrate(Poly<R, C>& P, const ClipParams& cp, cons
         P.fent[atomicAdd(&P.fend[c], 1u)] = a | (b << 8) | sv;
     }
     __syncwarp();
-#pragma unroll
-    for (int k = 0; k < FPL; k++) {
-        const int f = lane + 32 * k;
-        if (32 * k >= np) break;  // warp-uniform
-        const int m = fcount[k];
-        if (f >= np || m == 0) continue;
+    int nf = 0;  // facets among this lane's faces
+#pragma unroll 1
+    for (int f = lane; f < np; f += 32) {
+        const int e0 = f > 0 ? (int)P.fend[f - 1] : 0;
+        const int m = (int)P.fend[f] - e0;
+        P.fa[f] = R(-1);
+        if (m == 0) continue;
         if (m < 3) {
             bad = true;
             continue;
         }
-        const int e0 = (int)P.fend[f] - m;
         // fan apex: the entry of the lowest vertex slot
         int first = e0;
         for (int e = e0 + 1; e < e0 + m; e++)
@@ -1263,13 +1271,8 @@ __device__ __noinline__ bool integrate(Poly<R, C>& P, const ClipParams& cp, cons
         sy += ay2;
         sz += az2;
         sabs += A;
-        const int32_t j = P.pj[f];
-        if (j >= 0 && A > R(0)) {
-            if (nf < FPL) {
-                fj[nf] = j;
-                fc[nf] = (double)(A / P.plen[f]) * cp.a;
-                fslot[nf] = f;
-            }
+        if (P.pj[f] >= 0 && A > R(0)) {
+            P.fa[f] = A / P.plen[f];
             nf++;
         }
     }
@@ -1281,7 +1284,7 @@ __device__ __noinline__ bool integrate(Poly<R, C>& P, const ClipParams& cp, cons
     sy = warp_sum_r(sy);
     sz = warp_sum_r(sz);
     sabs = warp_sum_r(sabs);
-    // facets
+    // facets, in the order lane by lane, then this lane's faces in slot order
     int incl = nf;
     for (int q = 1; q < 32; q <<= 1) {
         const int y = __shfl_up_sync(FULLMASK, incl, q);
@@ -1291,22 +1294,28 @@ __device__ __noinline__ bool integrate(Poly<R, C>& P, const ClipParams& cp, cons
     // plane slot -> index in [the 6 box planes, then the facets as written], for the
     // stored topology (0xff: the slot has no facet)
     uint8_t* map = P.fmap;
-    for (int f = lane; f < P.np; f += 32) map[f] = f < 6 ? (uint8_t)f : (uint8_t)0xff;
+#pragma unroll 1
+    for (int f = lane; f < np; f += 32) map[f] = f < 6 ? (uint8_t)f : (uint8_t)0xff;
     __syncwarp();
     if (total > FCAP) {
         st |= CS_CAPACITY | CS_CAP_FACE;
     } else {
-        const int pos = incl - nf;
-        for (int q = 0; q < nf && q < FPL; q++) {
-            cp.fcol[i * FCAP + pos + q] = fj[q];
-            cp.fval[i * FCAP + pos + q] = fc[q];
-            map[fslot[q]] = (uint8_t)(6 + pos + q);
+        int pos = incl - nf;
+#pragma unroll 1
+        for (int f = lane; f < np; f += 32) {
+            const R c = P.fa[f];
+            if (!(c >= R(0))) continue;
+            cp.fcol[i * FCAP + pos] = P.pj[f];
+            cp.fval[i * FCAP + pos] = (double)c * cp.a;
+            map[f] = (uint8_t)(6 + pos);
+            pos++;
         }
     }
     __syncwarp();
     // the topology: every vertex as three indices into that list (kept only when
     // every plane a vertex uses is a box plane or a facet, and the counts fit)
     bool tok = total <= FCAP && 6 + total <= CapS::MP && nt <= TOPO;
+#pragma unroll 1
     for (int s2 = lane; s2 < nt && tok; s2 += 32) {
         const uint32_t t = P.tri[s2];
         const uint32_t a = map[t & 0xff], b2 = map[(t >> 8) & 0xff], c = map[(t >> 16) & 0xff];
@@ -1317,7 +1326,7 @@ __device__ __noinline__ bool integrate(Poly<R, C>& P, const ClipParams& cp, cons
     const R closure = sqrt(sx * sx + sy * sy + sz * sz);
     const R tol = sizeof(R) == 4 ? R(1e-4) : R(1e-10);
     if (!(closure <= tol * sabs)) bad = true;
-    const double vol = vol6 / 6.0;
+    const double vol = vol6 * (1.0 / 6.0);
     if (!(vol > 0.0) || !isfinite(vol)) bad = true;
     // first moment about the seed = moment about o + (z + o) V (mx.. hold 24 x moment
     // about o; o is relative to the frame origin z)
@@ -1326,10 +1335,13 @@ __device__ __noinline__ bool integrate(Poly<R, C>& P, const ClipParams& cp, cons
     mz += 24.0 * (fr.zd[2] + (double)o[2]) * vol;
     bad = __any_sync(FULLMASK, bad);
     st = __reduce_or_sync(FULLMASK, st);
-    const double mm[3] = {mx / 24.0, my / 24.0, mz / 24.0};
+    const double mm[3] = {mx * (1.0 / 24.0), my * (1.0 / 24.0), mz * (1.0 / 24.0)};
     const bool valid = vol > 0.0 && isfinite(vol);
-    if (valid)
-        for (int a = 0; a < 3; a++) cen[a] = (float)(mm[a] / vol);
+    if (valid) {
+        // the centroid is kept in FP32 (frame anchor): one FP32 division per axis
+        const float fv = (float)vol;
+        for (int a = 0; a < 3; a++) cen[a] = (float)mm[a] / fv;
+    }
     if (lane == 0) {
         const double a3 = cp.a * cp.a * cp.a;
         const double a4 = a3 * cp.a;
@@ -1414,6 +1426,7 @@ __device__ __noinline__ bool topo_init(Poly<R, C>& P, const ClipParams& cp, cons
     if (6 + nf > C::MP || nt > C::MT || nt > TOPO || nt < 4) return false;
     poly_init(P, cp, cc.fr.z, lane);  // the box planes in slots 0..5
     bool ok = true;
+#pragma unroll 1
     for (int k = lane; k < nf; k += 32) {
         const int32_t j = cp.fcol[cc.i * FCAP + k];
         V4<R> pn;
@@ -1428,6 +1441,7 @@ __device__ __noinline__ bool topo_init(Poly<R, C>& P, const ClipParams& cp, cons
     __syncwarp();
     const R dtol = sizeof(R) == 4 ? R(1e-3) : R(1e-6);
     const uint32_t npl = (uint32_t)(6 + nf);
+#pragma unroll 1
     for (int s = lane; s < nt; s += 32) {
         const uint32_t t = cp.topo[cc.i * TOPO + s];
         const uint32_t a = t & 0xff, b = (t >> 8) & 0xff, c = (t >> 16) & 0xff;
@@ -1435,14 +1449,15 @@ __device__ __noinline__ bool topo_init(Poly<R, C>& P, const ClipParams& cp, cons
             ok = false;
             continue;
         }
-        R det_rel;
-        const V3<R> v = vertex_of(P, t, det_rel);
-        if (!(det_rel > dtol) || !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z))) ok = false;
+        bool well;
+        const V3<R> v = vertex_of(P, t, dtol, well);
+        if (!well || !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z))) ok = false;
         P.tri[s] = t;
         set_vert(P, s, v);
     }
     ok = __all_sync(FULLMASK, ok);
     if (!ok) return false;
+#pragma unroll 1
     for (int s = lane; s < nt; s += 32) {
         const V3<R> v = vert(P, s);
         const uint32_t t = P.tri[s];
