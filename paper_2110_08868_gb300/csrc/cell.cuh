@@ -1537,7 +1537,11 @@ __device__ __forceinline__ void process_cell(Poly<R, C>& P, const ClipParams& cp
         b.psi_i = cc.si.phi;
         poly_bounds(P, cp, b, lane);
         bool done = true;
-        if (MODE == MODE_FULL) done = ring_walk(P, cp, cc, b, zprev, lane, bad, st);
+        // near-first rings for cells clipped from a list; a warm-started cell of the
+        // FP64 re-clip already holds the FP32 pass's polytope, and the pyramid walk
+        // below clips every seed that cuts whatever the order
+        if (MODE == MODE_FULL && !(warm && cp.pass == 3))
+            done = ring_walk(P, cp, cc, b, zprev, lane, bad, st);
         if (done) done = traverse<R, C, MODE>(P, cp, cc, b, lane, bad, st);
         if (!done && MODE == MODE_CERTIFY && (st & CS_UNCERTIFIED)) {
 #ifdef SDOT_COUNTERS
@@ -1597,7 +1601,16 @@ __device__ __forceinline__ void process_cell(Poly<R, C>& P, const ClipParams& cp
             cp.vol[i] = 0.0;
             cp.m1[3 * i] = cp.m1[3 * i + 1] = cp.m1[3 * i + 2] = 0.0;
         }
-        if (st & (CS_EMPTY | CS_CAPACITY | CS_INCONSISTENT)) cp.topo_n[i] = 0;
+        // FP32 cells failing a check, and cells over the small capacity, are clipped
+        // again in FP64 (small polytope first, the large one for its overflows)
+        const bool redo = !BIG && (((sizeof(R) == 4) && (st & CS_INCONSISTENT)) ||
+                                   (st & CS_CAPACITY));
+        // the topology stays only where it is whole: an FP32 cell sent to the FP64
+        // re-clip keeps it as that pass's warm start, which validates it in FP64
+        const bool keep_topo =
+            !(st & (CS_EMPTY | CS_CAPACITY)) &&
+            (!(st & CS_INCONSISTENT) || (redo && (st & CS_INCONSISTENT) == st));
+        if (!keep_topo) cp.topo_n[i] = 0;
         // history of the evaluation kept in the final status: a cell of the re-queue
         // pass was re-queued (8); a cell of the FP64 re-clip keeps what sent it there
         // (4: FP32 check failed, 32/64/128: small capacity exceeded) and its re-queue
@@ -1607,10 +1620,6 @@ __device__ __forceinline__ void process_cell(Poly<R, C>& P, const ClipParams& cp
             hist = cp.status[i] & (CS_INCONSISTENT | CS_UNCERTIFIED | CS_CAP_POLY | CS_CAP_FACE |
                                    CS_CAP_STACK);
         cp.status[i] = (uint8_t)(st | hist);
-        // FP32 cells failing a check, and cells over the small capacity, are clipped
-        // again in FP64 (small polytope first, the large one for its overflows)
-        const bool redo = !BIG && (((sizeof(R) == 4) && (st & CS_INCONSISTENT)) ||
-                                   (st & CS_CAPACITY));
         if (redo) {
             const int32_t q = atomicAdd(cp.q64_cnt, 1);
             cp.q64_out[q] = (int32_t)i;
