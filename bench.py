@@ -374,6 +374,16 @@ def run_native(args, rank, world, local):
             e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps, dist)
             e2e = {"value": world * N / (e_ms / 1e3), "unit": "cells/s",
                    "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N + 24 * N}
+        # the same calls on a context that carries no certificates (every cell walks)
+        rc, ctx3 = B.sdot_create(pos_dev, None, box,
+                                 B.sdot_default_options(precision=args.precision,
+                                                        carry_certificates=0))
+        B.check(rc)
+        try:
+            eval_steps(B, ctx3, psis, vol, cen, hcsr, 3, stream)
+            ms3, info3 = eval_steps(B, ctx3, psis, vol, cen, hcsr, 4, stream)
+        finally:
+            B.sdot_destroy(ctx3)
     finally:
         B.sdot_destroy(ctx)
 
@@ -419,8 +429,11 @@ def run_native(args, rank, world, local):
              "cells_per_s_median": N / (statistics.median(ms_each) / 1e3),
              "eval_detail": {"requeued": [x["requeued"] for x in info][:4],
                              "reclipped_fp64": [x["reclipped_fp64"] for x in info][:4],
+                             "carried": [x["carried"] for x in info][:4],
                              "ms_pass_median": [statistics.median(x["ms_pass"][q] for x in info)
                                                 for q in range(3)]},
+             "cells_per_s_walk_only": N / (statistics.median(ms3) / 1e3),
+             "ms_pass1_walk_only": statistics.median(x["ms_pass"][0] for x in info3),
              "hess_nnz": hess_nnz,
              "roofline_cg": cg}
     if not args.no_fp64_compare:
@@ -448,7 +461,10 @@ def run_native(args, rank, world, local):
                        "tol": args.tol, "k": 24,
                        "step": "one sdot_laguerre (volumes, centroids, CSR Hessian) at the "
                                "converged weights of the solve to tol, alternating with its "
-                               "continuation to tol/10; kNN excluded",
+                               "continuation to tol/10; kNN excluded; every cell certified, "
+                               "by its security walk or by the certificate carried from the "
+                               "previous call (extra.eval_detail.carried cells; "
+                               "extra.cells_per_s_walk_only with carrying off)",
                        "l2": "inputs larger than L2 (device working set >> 129 MB)",
                        "parallelism": "replicas" if world > 1 else "1 GPU"},
             "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "roofline": roofline,

@@ -66,6 +66,11 @@ typedef struct {
     int verbose;           /* 1: one JSON line per Newton iteration on stderr */
     int warm_alpha;        /* 1 (default): each line search starts at min(1, 4 alpha_prev)
                               instead of 1; 0: always 1, 1/2, 1/4, ... */
+    int carry_certificates; /* 1 (default): a cell's security walk is replaced by the
+                              certificate of its previous walk while that still holds
+                              (psi_j - psi_i moved by less than 0.01 a^2 and the cell by
+                              less than 0.01 a; the seeds within those reserves are
+                              re-tested exactly); 0: every evaluation walks every cell */
 } sdot_options;
 
 /* The Hessian in CSR form. L = -Hessian(K) is the weighted graph Laplacian
@@ -117,6 +122,10 @@ typedef struct {
     double l2_err;           /* ||V - nu||_2 */
     double min_vol;          /* min_j V_j */
     int precision;           /* SDOT_PREC_* of the clipping */
+    int64_t carried;         /* cells whose security walk a carried certificate replaced:
+                                the previous evaluation's walk, with reserves of 0.01 a in
+                                the cell's bounds and 0.01 a^2 in the change of psi_j -
+                                psi_i, plus an exact re-test of the seeds within them */
 } sdot_eval_info;
 
 typedef struct sdot_ctx sdot_ctx;

@@ -36,7 +36,7 @@ class sdot_options(ctypes.Structure):
                 ("seeds_per_leaf", ctypes.c_double), ("cg_rtol", ctypes.c_double),
                 ("cg_maxit", ctypes.c_int), ("newton_maxit", ctypes.c_int),
                 ("alpha_min", ctypes.c_double), ("verbose", ctypes.c_int),
-                ("warm_alpha", ctypes.c_int)]
+                ("warm_alpha", ctypes.c_int), ("carry_certificates", ctypes.c_int)]
 
 
 class sdot_csr(ctypes.Structure):
@@ -67,7 +67,7 @@ class sdot_eval_info(ctypes.Structure):
                 ("requeued", ctypes.c_int64), ("reclipped_fp64", ctypes.c_int64),
                 ("n_empty", ctypes.c_int64), ("max_rel_err", ctypes.c_double),
                 ("l2_err", ctypes.c_double), ("min_vol", ctypes.c_double),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("carried", ctypes.c_int64)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}

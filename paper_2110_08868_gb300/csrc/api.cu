@@ -135,6 +135,7 @@ int check_opt(const sdot_options& o) {
     if (!(o.cg_rtol > 0 && o.cg_rtol < 1)) return SDOT_ERR_ARG;
     if (o.cg_maxit < 1 || o.newton_maxit < 0) return SDOT_ERR_ARG;
     if (!(o.alpha_min > 0 && o.alpha_min <= 1)) return SDOT_ERR_ARG;
+    if (o.carry_certificates != 0 && o.carry_certificates != 1) return SDOT_ERR_ARG;
     return SDOT_OK;
 }
 
@@ -246,6 +247,9 @@ int alloc_context(sdot_ctx* c) {
         (rc = alloc_n(c, &d.status, N)) || (rc = alloc_n(c, &d.fcnt, N)) ||
         (rc = alloc_n(c, &d.fcol, N * FCAP)) || (rc = alloc_n(c, &d.fval, N * FCAP)) ||
         (rc = alloc_n(c, &d.topo, N * TOPO)) || (rc = alloc_n(c, &d.topo_n, N)) ||
+        (rc = alloc_n(c, &d.cert_f, N * CERT_F)) || (rc = alloc_n(c, &d.cert_s, N * CERT_S)) ||
+        (rc = alloc_n(c, &d.cert_j, N * CERT_NEAR)) || (rc = alloc_n(c, &d.cert_n, N)) ||
+        (rc = alloc_n(c, &d.psi_prev, N)) ||
         (rc = alloc_n(c, &d.queue, N)) || (rc = alloc_n(c, &d.queue64, N)) ||
         (rc = alloc_n(c, &d.counters, 32)) || (rc = alloc_n(c, &d.row_ptr, N + 1)) ||
         (rc = alloc_n(c, &d.rowcnt, N + 1)) || (rc = alloc_n(c, &d.x, N)) ||
@@ -340,6 +344,7 @@ int create_context(const double* pos, const double* mass, int64_t N, const doubl
     memset(&d, 0, sizeof d);
     d.N = N;
     d.k = c->opt.k;
+    d.carry = c->opt.carry_certificates;
     for (int a = 0; a < 3; a++) d.L[a] = box[a];
     const double boxvol = box[0] * box[1] * box[2];
     d.a = cbrt(boxvol / (double)N);
@@ -401,6 +406,8 @@ int create_context(const double* pos, const double* mass, int64_t N, const doubl
         cudaMemsetAsync(d.fcol, 0, (size_t)N * FCAP * 4, s) != cudaSuccess ||
         cudaMemsetAsync(d.fval, 0, (size_t)N * FCAP * 8, s) != cudaSuccess ||
         cudaMemsetAsync(d.topo_n, 0, (size_t)N, s) != cudaSuccess ||
+        cudaMemsetAsync(d.cert_n, 0xff, (size_t)N, s) != cudaSuccess ||
+        cudaMemsetAsync(d.psi_prev, 0, (size_t)N * 8, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
         set_error("sdot_create: initialisation failed");
         return fail(SDOT_ERR_CUDA);
@@ -468,6 +475,7 @@ int sdot_default_options(sdot_options* o) {
     o->alpha_min = 1.0 / (1 << 30);
     o->verbose = 0;
     o->warm_alpha = 1;
+    o->carry_certificates = 1;
     return SDOT_OK;
 }
 
@@ -564,6 +572,7 @@ int sdot_last_eval(const sdot_ctx* c, sdot_eval_info* info) {
     info->l2_err = r.l2_err;
     info->min_vol = r.min_vol;
     info->precision = c->last_prec;
+    info->carried = r.carried;
     return SDOT_OK;
 }
 

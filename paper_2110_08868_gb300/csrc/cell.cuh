@@ -28,6 +28,7 @@
 // (ball and bounding-box support, then an exact vertex classification).
 #pragma once
 
+#include <cuda_fp16.h>
 #include <float.h>
 #include <math.h>
 
@@ -83,7 +84,10 @@ struct Poly {
     };
     float sup[27];            // support max_v v.u over the 26 stencil directions u
     int np, nt;
+    int ncert;                // seeds recorded for the cell's certificate (-1: too many)
+#ifdef SDOT_COUNTERS
     uint32_t wc[8];           // work counters of the current cell (diagnostic builds)
+#endif
 };
 
 // Work counters, compiled in only with -DSDOT_COUNTERS (diagnostic builds). The
@@ -141,6 +145,14 @@ struct ClipParams {
     uint8_t* topo_n;                 // N stored vertex counts (0: none)
     float nsz[MAXLEV][3];            // node size per pyramid level, units of a
     int pass;                        // 1 security test, 2 re-queue, 3 FP64 re-clip
+    // carried security certificates (see process_cell)
+    float* cert_f;                   // N * CERT_F: ball centre, radius, M and w reserves
+    uint16_t* cert_s;                // N * CERT_S: inflated supports, FP16 rounded up
+    int32_t* cert_j;                 // N * CERT_NEAR: seeds to re-test
+    uint8_t* cert_n;                 // N: their count, 0xff: no certificate
+    const uint32_t* cert_dpsi;       // ordered max and min of psi - psi_prev (a^2)
+    int32_t* cert_carried;           // cells certified by a carried certificate
+    int cert_use;                    // record and use certificates (first pass)
 };
 
 __device__ __forceinline__ double wrapd(double dx, double L, double halfL) {
@@ -849,6 +861,57 @@ __device__ __forceinline__ bool support_may_cut(const float* sup, const Bounds& 
     return cn + rn > w - margin2;
 }
 
+// Carried security certificates. A pass-1 walk that certifies a cell records, besides
+// the cell itself, a certificate for later evaluations: the walk's node tests use the
+// ball inflated by CERT_EPS and M inflated by CERT_ETA, and every seed that is not a
+// plane of the cell and passes the prefilter inflated the same way (supports + CERT_EPS
+// rounded up to FP16, ball radius + CERT_EPS, offset w - CERT_ETA) is recorded for an
+// exact re-test. At a later evaluation the certificate holds, and the walk is skipped,
+// when the warm-started polytope lies inside the stored ball and below the stored
+// supports, its M fits the stored M less the change of psi differences since, the
+// stored w reserve covers that change, and no recorded seed cuts it exactly: every seed
+// a node test excluded still satisfies 1/2 (u - R)_+^2 >= M + psi_j - psi_i, and every
+// seed the inflated prefilter excluded still has its plane beyond the stored supports.
+constexpr float CERT_EPS = 0.01f;  // ball radius and support reserve, units of a
+constexpr float CERT_ETA = 0.01f;  // reserve for the change of psi_j - psi_i, units of a^2
+
+// inflated support of direction k as stored (FP16, rounded up)
+__device__ __forceinline__ float cert_sup(const float* sup, int k) {
+    return __half2float(__float2half_ru(__fadd_ru(sup[k], CERT_EPS)));
+}
+
+// The prefilter of support_may_cut on the inflated certificate quantities.
+__device__ __forceinline__ bool cert_may_cut(const float* sup, const Bounds& b, float nx,
+                                             float ny, float nz, float w) {
+    float m[3] = {fabsf(nx), fabsf(ny), fabsf(nz)};
+    int code[3] = {nx >= 0.f ? 1 : -1, ny >= 0.f ? 3 : -3, nz >= 0.f ? 9 : -9};
+#define SDOT_CX(i, j)                                  \
+    if (m[i] < m[j]) {                                 \
+        const float tm = m[i];                         \
+        m[i] = m[j];                                   \
+        m[j] = tm;                                     \
+        const int tc = code[i];                        \
+        code[i] = code[j];                             \
+        code[j] = tc;                                  \
+    }
+    SDOT_CX(0, 1)
+    SDOT_CX(1, 2)
+    SDOT_CX(0, 1)
+#undef SDOT_CX
+    const int k1 = 13 + code[0], k2 = k1 + code[1], k3 = k2 + code[2];
+    const float t3 = m[2] * cert_sup(sup, k3), t2 = (m[1] - m[2]) * cert_sup(sup, k2),
+                t1 = (m[0] - m[1]) * cert_sup(sup, k1);
+    const float wr = __fsub_rd(w, CERT_ETA);
+    const float S = t1 + t2 + t3;
+    const float margin = 2e-5f * (fabsf(t1) + fabsf(t2) + fabsf(t3) + fabsf(wr)) + 1e-5f;
+    if (!(S > wr - margin)) return false;
+    const float R = __fadd_ru(b.Rc, CERT_EPS);
+    const float cn = b.c[0] * nx + b.c[1] * ny + b.c[2] * nz;
+    const float rn = R * sqrtf(nx * nx + ny * ny + nz * nz);
+    const float margin2 = 2e-5f * (fabsf(cn) + rn + fabsf(wr)) + 1e-5f;
+    return cn + rn > wr - margin2;
+}
+
 enum { MODE_CERTIFY = 0, MODE_FULL = 1 };
 enum { LEAF_OK = 0, LEAF_STOP = 1 };
 
@@ -920,6 +983,8 @@ __device__ __noinline__ int process_leaves(Poly<R, C>& P, const ClipParams& cp,
     const int total = __shfl_sync(FULLMASK, incl, 31);
     const int excl = incl - n;
     WCOUNT(P, 4, total);
+    // a certifying walk of the first pass records the cell's certificate
+    const bool rec = MODE == MODE_CERTIFY && cp.pass == 1 && cp.cert_use;
     for (int base = 0; base < total; base += 32) {
         const int t = base + lane;
         // the lane q owning flattened seed t: the first with incl[q] > t
@@ -932,21 +997,39 @@ __device__ __noinline__ int process_leaves(Poly<R, C>& P, const ClipParams& cp,
         const int ex = __shfl_sync(FULLMASK, excl, q);
         const int32_t s0 = __shfl_sync(FULLMASK, sb, q);
         const int32_t s = s0 + (t - ex);
-        bool cand = false;
+        bool cand = false, nearb = false;
         if (t < total && s != (int32_t)cc.i) {
             float nx, ny, nz, w;
             plane_f32(cp, cc.si, s, nx, ny, nz, w);
             cand = support_may_cut(P.sup, b, nx, ny, nz, w);
+            if (rec) nearb = cand || cert_may_cut(P.sup, b, nx, ny, nz, w);
         }
         uint32_t cm = __ballot_sync(FULLMASK, cand);
+        uint32_t nm = rec ? __ballot_sync(FULLMASK, nearb) : cm;
         WCOUNT(P, 5, __popc(cm));
-        if (!cm) continue;
+        if (!nm) continue;
         // drop the seeds that already are planes of the polytope (the cell's own facet
         // neighbours pass the prefilter), then build the exact planes of the rest
-        for (uint32_t m2 = cm; m2;) {
+        for (uint32_t m2 = nm; m2;) {
             const int src = __ffs(m2) - 1;
             m2 &= m2 - 1;
-            if (has_plane(P, __shfl_sync(FULLMASK, s, src), lane)) cm &= ~(1u << src);
+            if (has_plane(P, __shfl_sync(FULLMASK, s, src), lane)) {
+                cm &= ~(1u << src);
+                nm &= ~(1u << src);
+            }
+        }
+        // the certificate's seeds to re-test (P.ftri is free during a certifying walk)
+        if (rec && nm) {
+            const int n0 = P.ncert;
+            const int k = __popc(nm);
+            __syncwarp();
+            if (n0 >= 0 && n0 + k <= CERT_NEAR) {
+                if ((nm >> lane) & 1u) P.ftri[n0 + __popc(nm & lanes_below(lane))] = (uint32_t)s;
+                if (lane == 0) P.ncert = n0 + k;
+            } else if (lane == 0) {
+                P.ncert = -1;
+            }
+            __syncwarp();
         }
         if (!cm) continue;
         cand = (cm >> lane) & 1u;
@@ -1042,6 +1125,11 @@ __device__ __noinline__ bool traverse(Poly<R, C>& P, const ClipParams& cp, const
     int sp = 1;
     const float Lt[3] = {cp.Lt[0], cp.Lt[1], cp.Lt[2]};
     WalkBall wb = walk_ball(b);
+    if (MODE == MODE_CERTIFY && cp.pass == 1 && cp.cert_use) {
+        // the certificate's reserves (the same roundings as cert_store)
+        wb.Rc = __fadd_ru(wb.Rc, CERT_EPS);
+        wb.Mv = __fadd_ru(wb.Mv, CERT_ETA);
+    }
     __syncwarp();
     while (sp > 0) {
         const uint32_t e = P.stack[sp - 1];
@@ -1486,12 +1574,87 @@ __device__ __forceinline__ float top_psimax(const ClipParams& cp, int lane) {
     return warp_max(m);
 }
 
+// The cell's carried certificate against its warm-started polytope (bounds b): true when
+// it still certifies the cell (see CERT_EPS above). The reserves it used are then written
+// back, less the change of psi differences of this evaluation.
+template <typename R, class C>
+__device__ __noinline__ bool cert_check(Poly<R, C>& P, const ClipParams& cp, const CellCtx& cc,
+                                        const Bounds& b, int64_t i, int nc, int lane) {
+    const float* cf = cp.cert_f + i * CERT_F;
+    const float c0 = cf[0], c1 = cf[1], c2 = cf[2], Rt = cf[3], Mr = cf[4], Wr = cf[5];
+    const float hi = ord2f(cp.cert_dpsi[0]), lo = ord2f(cp.cert_dpsi[1]);
+    const float cons = __fadd_ru(__fsub_ru(hi, lo), 1e-6f);
+    const float Mn = __fsub_rd(Mr, cons), Wn = __fsub_rd(Wr, cons);
+    bool ok = nc <= CERT_NEAR && cons >= 0.f && Wn >= 0.f && b.Mv <= Mn;
+    // below the stored supports (lane k: direction k)
+    if (lane < 27 && lane != 13) {
+        const float S = __half2float(__ushort_as_half(cp.cert_s[i * CERT_S + lane]));
+        if (!(P.sup[lane] <= S - 1e-5f)) ok = false;
+    }
+    // inside the stored ball
+    float r2 = 0.f;
+#pragma unroll 1
+    for (int s = lane; s < P.nt; s += 32) {
+        const float dx = ((float)P.vx[s] + b.zf[0]) - c0;
+        const float dy = ((float)P.vy[s] + b.zf[1]) - c1;
+        const float dz = ((float)P.vz[s] + b.zf[2]) - c2;
+        r2 = fmaxf(r2, dx * dx + dy * dy + dz * dz);
+    }
+    r2 = warp_max(r2);
+    if (!(sqrtf(r2) * (1.f + 1e-6f) + 1e-5f <= Rt)) ok = false;
+    if (!__all_sync(FULLMASK, ok)) return false;
+    // the recorded seeds, tested exactly as the walk tests a candidate
+    V4<R> pl;
+    pl.x = pl.y = pl.z = pl.w = R(0);
+    R len = R(1);
+    const bool have = lane < nc;
+    if (have) {
+        const int32_t j = cp.cert_j[i * CERT_NEAR + lane];
+        if (j >= 0 && j < cp.N && j != (int32_t)cc.i) build_plane(cp, cc, j, pl, len);
+        else ok = false;
+    }
+    if (!__all_sync(FULLMASK, ok)) return false;
+    for (uint32_t m = __ballot_sync(FULLMASK, have); m;) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1;
+        const V4<R> pn = shfl_plane(pl, src);
+        const R plen = __shfl_sync(FULLMASK, len, src);
+        if (poly_cut_by(P, pn, plen, lane)) return false;
+    }
+    if (lane == 0) {
+        cp.cert_f[i * CERT_F + 4] = Mn;
+        cp.cert_f[i * CERT_F + 5] = Wn;
+    }
+    return true;
+}
+
+// Record the certificate of a certifying walk (bounds b before the walk, the seeds in
+// P.ftri); its count is set once the cell's outputs are known to be clean.
+template <typename R, class C>
+__device__ __noinline__ void cert_store(const Poly<R, C>& P, const ClipParams& cp, const Bounds& b,
+                                        int64_t i, int lane) {
+    if (lane < 27)
+        cp.cert_s[i * CERT_S + lane] =
+            lane == 13 ? (uint16_t)0 : __half_as_ushort(__float2half_ru(__fadd_ru(P.sup[lane], CERT_EPS)));
+    const int n = P.ncert;
+    if (lane < n) cp.cert_j[i * CERT_NEAR + lane] = (int32_t)P.ftri[lane];
+    if (lane == 0) {
+        float* cf = cp.cert_f + i * CERT_F;
+        cf[0] = b.c[0];
+        cf[1] = b.c[1];
+        cf[2] = b.c[2];
+        cf[3] = __fadd_ru(b.Rc, CERT_EPS);
+        cf[4] = __fadd_ru(b.Mv, CERT_ETA);
+        cf[5] = CERT_ETA;
+    }
+}
+
 // One work item w of a clipping pass: cell worklist[w] (or w), clipped by its first
 // candidates, certified (pass 1) or walked (re-queue pass), integrated; outputs
 // written, the cell queued for the next pass where needed. BIG: the large-capacity
 // FP64 re-clip, after which no pass follows.
 template <typename R, class C, int MODE>
-__device__ __forceinline__ void process_cell(Poly<R, C>& P, const ClipParams& cp, int64_t w,
+__device__ __forceinline__ bool process_cell(Poly<R, C>& P, const ClipParams& cp, int64_t w,
                                              float psimax_glob, float halfLmin, int lane) {
     constexpr bool BIG = C::MP > CapS::MP;
     CellCtx cc;
@@ -1528,6 +1691,11 @@ __device__ __forceinline__ void process_cell(Poly<R, C>& P, const ClipParams& cp
     }
     if (rc == CLIP_EMPTY) st |= CS_EMPTY;
     if (rc == CLIP_CAP) st |= CS_CAPACITY | CS_CAP_POLY;
+    // a certifying first pass carries the cell's security certificate between
+    // evaluations (see CERT_EPS): used when it still holds, recorded after a walk
+    const bool rec = MODE == MODE_CERTIFY && cp.pass == 1 && cp.cert_use;
+    bool carried = false, stored = false, reframed = false;
+    int ncert = -1;
     if (!st) {
         Bounds b;
         for (int a = 0; a < 3; a++) {
@@ -1536,13 +1704,31 @@ __device__ __forceinline__ void process_cell(Poly<R, C>& P, const ClipParams& cp
         }
         b.psi_i = cc.si.phi;
         poly_bounds(P, cp, b, lane);
+        if (rec && warm) {
+            const int nc = cp.cert_n[i];
+            if (nc != 0xff) carried = cert_check(P, cp, cc, b, i, nc, lane);
+        }
         bool done = true;
-        // near-first rings for cells clipped from a list; a warm-started cell of the
-        // FP64 re-clip already holds the FP32 pass's polytope, and the pyramid walk
-        // below clips every seed that cuts whatever the order
-        if (MODE == MODE_FULL && !(warm && cp.pass == 3))
-            done = ring_walk(P, cp, cc, b, zprev, lane, bad, st);
-        if (done) done = traverse<R, C, MODE>(P, cp, cc, b, lane, bad, st);
+        if (!carried) {
+            if (rec) {
+                if (lane == 0) P.ncert = 0;
+                __syncwarp();
+            }
+            // near-first rings for cells clipped from a list; a warm-started cell of the
+            // FP64 re-clip already holds the FP32 pass's polytope, and the pyramid walk
+            // below clips every seed that cuts whatever the order
+            if (MODE == MODE_FULL && !(warm && cp.pass == 3))
+                done = ring_walk(P, cp, cc, b, zprev, lane, bad, st);
+            if (done) done = traverse<R, C, MODE>(P, cp, cc, b, lane, bad, st);
+            if (done && rec) {
+                __syncwarp();
+                ncert = P.ncert;
+                if (ncert >= 0) {
+                    cert_store(P, cp, b, i, lane);
+                    stored = true;
+                }
+            }
+        }
         if (!done && MODE == MODE_CERTIFY && (st & CS_UNCERTIFIED)) {
 #ifdef SDOT_COUNTERS
             __syncwarp();
@@ -1553,8 +1739,9 @@ __device__ __forceinline__ void process_cell(Poly<R, C>& P, const ClipParams& cp
                 const int32_t q = atomicAdd(cp.queue_cnt, 1);
                 cp.queue_out[q] = (int32_t)i;
                 cp.status[i] = (uint8_t)st;
+                cp.cert_n[i] = 0xff;
             }
-            return;
+            return false;
         }
     }
 #ifdef SDOT_COUNTERS
@@ -1576,6 +1763,7 @@ __device__ __forceinline__ void process_cell(Poly<R, C>& P, const ClipParams& cp
 #pragma unroll
         for (int a = 0; a < 3; a++) dz2 += (cen[a] - cc.fr.z[a]) * (cen[a] - cc.fr.z[a]);
         if (dz2 > REFRAME_DIST * REFRAME_DIST) {
+            reframed = true;
             __syncwarp();  // facets and counts written by integrate
             const int nf = min(cp.fcnt[i], FCAP);
             __syncwarp();
@@ -1624,7 +1812,13 @@ __device__ __forceinline__ void process_cell(Poly<R, C>& P, const ClipParams& cp
             const int32_t q = atomicAdd(cp.q64_cnt, 1);
             cp.q64_out[q] = (int32_t)i;
         }
+        // the certificate stays valid only for a clean cell whose every plane other
+        // than the box's is a facet (the planes of its next warm start)
+        const bool clean = rec && st == 0 && !reframed && cp.fcnt[i] == P.np - 6;
+        if (!clean || !(carried || stored)) cp.cert_n[i] = 0xff;
+        else if (stored) cp.cert_n[i] = (uint8_t)ncert;
     }
+    return carried;
 }
 
 }  // namespace sdot

@@ -35,13 +35,15 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK_CLIP * 32, (clip_min_blocks<R,
     Poly<R, C>& P = polys[threadIdx.x >> 5];
     const float psimax_glob = top_psimax(cp, lane);
     const float halfLmin = 0.5f * fminf(cp.Lt[0], fminf(cp.Lt[1], cp.Lt[2]));
+    int carried = 0;  // cells certified by a carried certificate
     while (true) {
         int64_t w = 0;
         if (lane == 0) w = atomicAdd(cp.work_counter, 1);
         w = __shfl_sync(FULLMASK, w, 0);
         if (w >= cp.nwork) break;
-        process_cell<R, C, MODE>(P, cp, w, psimax_glob, halfLmin, lane);
+        carried += process_cell<R, C, MODE>(P, cp, w, psimax_glob, halfLmin, lane) ? 1 : 0;
     }
+    if (lane == 0 && carried) atomicAdd(cp.cert_carried, carried);
 }
 
 // The same pass over the work items of several contexts in one persistent launch (a
@@ -141,8 +143,38 @@ __global__ void level_max_kernel(const float* __restrict__ in, int dx, int dy, i
     out[n] = m;
 }
 
+// Change of psi since the previous evaluation of the context: the largest and smallest
+// psi - psi_prev in units of a^2 (rounded outward, as order-preserving integers for the
+// atomics: mm[0] the maximum, mm[1] the minimum); psi_prev then takes psi. Only
+// differences of psi shape the diagram, so a carried certificate consumes max - min.
+__global__ void psi_change_kernel(const double* __restrict__ psi, double* __restrict__ prev,
+                                  int64_t N, double inv_a2, uint32_t* __restrict__ mm) {
+    float hi = -INFINITY, lo = INFINITY;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double p = psi[i];
+        const double dv = (p - prev[i]) * inv_a2;
+        hi = fmaxf(hi, __double2float_ru(dv));
+        lo = fminf(lo, __double2float_rd(dv));
+        prev[i] = p;
+    }
+    uint32_t h = f2ord(hi), l = f2ord(lo);
+    h = __reduce_max_sync(FULLMASK, h);
+    l = __reduce_min_sync(FULLMASK, l);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&mm[0], h);
+        atomicMin(&mm[1], l);
+    }
+}
+
 int build_pyramid(DeviceState& d, const double* psi, cudaStream_t s) {
     const int64_t N = d.N;
+    uint32_t* mm = reinterpret_cast<uint32_t*>(d.counters + 30);
+    SDOT_CUDA_TRY(cudaMemsetAsync(mm, 0, 4, s));
+    SDOT_CUDA_TRY(cudaMemsetAsync(mm + 1, 0xff, 4, s));
+    psi_change_kernel<<<2 * num_sms(), 256, 0, s>>>(psi, d.psi_prev, N, 1.0 / (d.a * d.a), mm);
+    note_launch();
+    SDOT_CUDA_TRY(cudaGetLastError());
     posf_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(
         d.pos, psi, N, 1.0 / d.a, 1.0 / (d.a * d.a), d.grid.h[0], d.grid.h[1], d.grid.h[2],
         d.grid.G[0], d.grid.G[1], d.grid.G[2], d.posf, d.pslo, d.leafc, d.ioff);
@@ -236,6 +268,49 @@ __global__ void cell_reduce_final(const double* __restrict__ part, int nb, doubl
     out[5] = (double)fl;
 }
 
+// Setup of a persistent clipping kernel, once per instantiation: blocks per SM from the
+// occupancy at the largest shared-memory carveout, then the smallest carveout that still
+// holds that many blocks, so the rest of the SM's memory stays L1 (which caches the
+// lanes' local memory). The occupancy is checked again at that carveout and the largest
+// one restored if it dropped.
+template <typename K>
+static cudaError_t clip_setup(K kernel, size_t smem, int* blocks) {
+    const int threads = WARPS_PER_BLOCK_CLIP * 32;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    int per_sm = 0;
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    int dev = 0, smem_sm = 0, resv = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) ==
+            cudaSuccess &&
+        cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev) ==
+            cudaSuccess &&
+        smem_sm > 0) {
+        // shared memory is allocated per block in 128-byte units, plus the reserved part;
+        // the percentage is rounded down and the driver rounds it up to a supported size
+        const size_t per_block = (smem + (size_t)resv + 127) / 128 * 128;
+        const int pct = (int)((size_t)per_sm * per_block * 100 / (size_t)smem_sm);
+        if (pct < 100 &&
+            cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct) ==
+                cudaSuccess) {
+            int again = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&again, kernel, threads, smem) !=
+                    cudaSuccess ||
+                again < per_sm)
+                cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        }
+        cudaGetLastError();
+    }
+    *blocks = per_sm * num_sms();
+    return cudaSuccess;
+}
+
 template <typename R, class C, int MODE>
 static int launch_clip(const ClipParams& cp, cudaStream_t s) {
     const size_t smem = sizeof(Poly<R, C>) * WARPS_PER_BLOCK_CLIP;
@@ -247,17 +322,7 @@ static int launch_clip(const ClipParams& cp, cudaStream_t s) {
     };
     static const Setup setup = [smem] {
         Setup u{0, cudaSuccess};
-        u.err = cudaFuncSetAttribute(clip_kernel<R, C, MODE>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (u.err == cudaSuccess)
-            u.err = cudaFuncSetAttribute(clip_kernel<R, C, MODE>,
-                                         cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        int per_sm = 0;
-        if (u.err == cudaSuccess)
-            u.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, clip_kernel<R, C, MODE>,
-                                                                  WARPS_PER_BLOCK_CLIP * 32, smem);
-        if (per_sm < 1) per_sm = 1;
-        u.blocks = per_sm * num_sms();
+        u.err = clip_setup(clip_kernel<R, C, MODE>, smem, &u.blocks);
         return u;
     }();
     if (setup.err != cudaSuccess) {
@@ -314,6 +379,13 @@ static ClipParams make_clip_params(DeviceState& d, const double* psi) {
     cp.fval = d.fval;
     cp.topo = d.topo;
     cp.topo_n = d.topo_n;
+    cp.cert_f = d.cert_f;
+    cp.cert_s = d.cert_s;
+    cp.cert_j = d.cert_j;
+    cp.cert_n = d.cert_n;
+    cp.cert_dpsi = reinterpret_cast<const uint32_t*>(d.counters + 30);
+    cp.cert_carried = d.counters + 29;
+    cp.cert_use = d.carry;
     cp.queue_out = d.queue;
     cp.queue_cnt = d.counters + 0;
     cp.q64_out = d.queue64;
@@ -337,6 +409,7 @@ int evaluate_cells(DeviceState& d, const double* psi, int precision, EvalResult*
     if (rc) return rc;
     ClipParams cp = make_clip_params(d, psi);
     SDOT_CUDA_TRY(cudaMemsetAsync(d.counters, 0, 8 * sizeof(int32_t), s));
+    SDOT_CUDA_TRY(cudaMemsetAsync(d.counters + 29, 0, sizeof(int32_t), s));
 
     cudaEvent_t e0, e1, ep1, ep2;
     cudaEventCreate(&e0);
@@ -407,6 +480,9 @@ int evaluate_cells(DeviceState& d, const double* psi, int precision, EvalResult*
     cudaEventElapsedTime(&res->ms_pass[1], ep1, ep2);
     cudaEventElapsedTime(&res->ms_pass[2], ep2, e1);
     SDOT_CUDA_TRY(cudaMemcpy(res->work, d.counters + 8, 64, cudaMemcpyDeviceToHost));
+    int32_t carried = 0;
+    SDOT_CUDA_TRY(cudaMemcpy(&carried, d.counters + 29, 4, cudaMemcpyDeviceToHost));
+    res->carried = carried;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaEventDestroy(ep1);
@@ -438,17 +514,7 @@ static int launch_clip_batch(const ClipBatch& bt, int64_t total, cudaStream_t s)
     };
     static const Setup setup = [smem] {
         Setup u{0, cudaSuccess};
-        u.err = cudaFuncSetAttribute(clip_batch_kernel<R, C, MODE>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (u.err == cudaSuccess)
-            u.err = cudaFuncSetAttribute(clip_batch_kernel<R, C, MODE>,
-                                         cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        int per_sm = 0;
-        if (u.err == cudaSuccess)
-            u.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &per_sm, clip_batch_kernel<R, C, MODE>, WARPS_PER_BLOCK_CLIP * 32, smem);
-        if (per_sm < 1) per_sm = 1;
-        u.blocks = per_sm * num_sms();
+        u.err = clip_setup(clip_batch_kernel<R, C, MODE>, smem, &u.blocks);
         return u;
     }();
     if (setup.err != cudaSuccess) {

@@ -33,6 +33,9 @@ constexpr int MAXP = 96;        // planes of the largest polytope (6 box planes 
 constexpr int MAXT = 192;       // vertices (dual triangles) of the largest polytope
 constexpr int FCAP = 64;        // facets stored per cell for the Hessian
 constexpr int TOPO = 64;        // vertices of a cell's stored topology (warm start)
+constexpr int CERT_NEAR = 16;   // seeds a carried security certificate re-tests exactly
+constexpr int CERT_F = 6;       // floats of a certificate: ball centre (3), radius, M, w reserve
+constexpr int CERT_S = 27;      // FP16 supports of a certificate (26 directions + unused centre)
 constexpr int MAXLEV = 8;       // pyramid levels
 
 // cell status bits (per cell, uint8)
@@ -77,6 +80,7 @@ struct DeviceState {
     uint4* ioff;              // offset in the grid cell as 32-bit fixed point (x, y, z, 0)
     int32_t* leafc;           // grid cell of each seed: x | y << 10 | z << 20
     int facets_valid;         // fcnt/fcol hold a complete previous diagram
+    int carry = 1;            // carry security certificates between evaluations
     int32_t* perm;            // sorted -> caller index
     int32_t* iperm;           // caller -> sorted index
     double* nu;               // masses (sorted)
@@ -96,6 +100,14 @@ struct DeviceState {
     uint32_t* topo;           // N * TOPO vertices of each cell as three plane indices
                               // (0..5 box faces, 6 + k facet k of fcol)
     uint8_t* topo_n;          // N vertex counts of topo (0: none stored)
+    // security certificates carried between evaluations (see process_cell): per cell the
+    // ball and reserves, the inflated supports, the seeds to re-test and their count
+    // (0xff: none); psi of the previous evaluation, for the change of psi since
+    float* cert_f;            // N * CERT_F
+    uint16_t* cert_s;         // N * CERT_S (FP16 bits, rounded up)
+    int32_t* cert_j;          // N * CERT_NEAR
+    uint8_t* cert_n;          // N
+    double* psi_prev;         // N
     int32_t* queue;           // N, re-queued cells
     int32_t* queue64;         // N, cells for the FP64 re-clip
     int32_t* counters;        // [0] requeue count [1] fp64 count [2] work counter
@@ -180,6 +192,7 @@ struct EvalResult {
     float ms;
     float ms_pass[3];             // certify pass, re-queue pass, FP64 re-clip pass
     unsigned long long work[8];   // diagnostic work counters (zero unless compiled in)
+    int64_t carried = 0;          // cells certified by a carried certificate (pass 1)
 };
 int build_pyramid(DeviceState& d, const double* psi, cudaStream_t s);
 int evaluate_cells(DeviceState& d, const double* psi, int precision, EvalResult* res,

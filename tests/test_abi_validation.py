@@ -24,6 +24,7 @@ def test_default_options():
     o = B.sdot_default_options()
     assert (o.k, o.precision, o.seeds_per_leaf, o.cg_rtol) == (24, B.SDOT_PREC_MIXED, 2.0, 1e-3)
     assert (o.cg_maxit, o.newton_maxit, o.warm_alpha, o.verbose) == (5000, 100, 1, 0)
+    assert o.carry_certificates == 1
     assert o.alpha_min == 2.0 ** -30
     so = B.sdot_server_default_options()
     assert (so.hbm_budget, so.max_active, so.device, so.batch_clip) == (0, 8, -1, 1)
@@ -46,7 +47,8 @@ def test_create_rejects_bad_boxes(box):
 @pytest.mark.parametrize("kw", [dict(k=0), dict(k=65), dict(precision=2),
                                 dict(seeds_per_leaf=0.0), dict(cg_rtol=0.0), dict(cg_rtol=1.0),
                                 dict(cg_maxit=0), dict(newton_maxit=-1), dict(alpha_min=0.0),
-                                dict(alpha_min=2.0)])
+                                dict(alpha_min=2.0), dict(carry_certificates=2),
+                                dict(carry_certificates=-1)])
 def test_create_rejects_bad_options(kw):
     rc, ctx = B.sdot_create(_pos(100), None, [1.0] * 3, B.sdot_default_options(**kw))
     assert rc == B.SDOT_ERR_ARG and not ctx.value
