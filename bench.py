@@ -49,10 +49,12 @@ N_SM = 152
 CG_BYTES_PER_ROW = 124
 # per off-diagonal entry of L: int32 column + FP32 weight
 CG_BYTES_PER_ENTRY = 8
-# DRAM bytes per launch from an ncu capture of the current kernels (None: not captured
-# since the kernel last changed)
-CLIP_TRAFFIC = None
-CG_TRAFFIC = None
+# DRAM bytes (read + write) per unit from ncu captures of the current kernels on the
+# clumpy 128^3 box (N = 2,202,087), scaled to a launch by the units it processes (None:
+# not captured since the kernel last changed): the first clipping pass per cell
+# (1.569 + 7.206 GB), one CG iteration (SpMV 402.4 MB + update 162.8 MB) per row
+CLIP_DRAM_PER_CELL = (1.569416e9 + 7.205903e9) / 2202087
+CG_DRAM_PER_ROW = (385.858560e6 + 16.551168e6 + 123.337216e6 + 39.467264e6) / 2202087
 
 
 def parse():
@@ -403,7 +405,8 @@ def run_native(args, rank, world, local):
         "clip_kernel<double,CapS,certify>"
     roofline = {"kernel": kname + " (first clipping pass)", "bound": "alu",
                 "launches_timed": len(pass1), "achieved": achieved_tf, "peak": peak_tf,
-                "unit": "TFLOP/s", "frac": achieved_tf / peak_tf, "traffic": CLIP_TRAFFIC,
+                "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
+                "traffic": None if CLIP_DRAM_PER_CELL is None else CLIP_DRAM_PER_CELL * N,
                 "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {clock_ghz:.3f} "
                                "GHz (median SM clock sampled under load)",
                 "per_launch_ms": pass1_ms, "flop_per_cell": FLOP_PER_CELL}
@@ -418,7 +421,8 @@ def run_native(args, rank, world, local):
         hbm = peaks.get("hbm_gbs", 6786.2)
         cg = {"kernel": "CG iteration (cg_spmv_kernel + cg_update_kernel)", "bound": "hbm",
               "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-              "traffic": CG_TRAFFIC, "per_iter_ms": it_ms, "bytes_per_iter": bytes_it,
+              "traffic": None if CG_DRAM_PER_ROW is None else CG_DRAM_PER_ROW * N,
+              "per_iter_ms": it_ms, "bytes_per_iter": bytes_it,
               "hess_slots": solve_st["hess_slots"], "hess_offdiag": solve_st["hess_offdiag"],
               "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     keep = ("newton_iters", "laguerre_evals", "cg_iters", "max_rel_err", "ms_knn", "ms_clip",
