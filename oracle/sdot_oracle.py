@@ -301,3 +301,36 @@ def deposit(pos, psi, box, M, lam, mass=None):
     if rc == -2:
         raise RuntimeError("oracle polytope capacity exceeded")
     return rho.reshape(M, M, M)
+
+
+def power_spectrum(rho, L, nbins=None):
+    """Power spectrum of the density contrast of a periodic M^3 mesh: the estimator
+    behind the fractional BAO signal d(k) = P_wig(k)/P_nw(k) - 1 (Sec. "BAO
+    reconstruction", Fig. 2).
+
+    delta = rho / mean(rho) - 1; delta_k = (sum_x delta(x) e^{-i k.x}) / M^3 over the
+    full complex FFT, k = 2 pi n / L with n the integer frequencies of numpy's fftfreq;
+    P(k) = L^3 |delta_k|^2. Mode n != 0 goes into bin b = floor(|n| + 1/2), kept for
+    1 <= b <= nbins (default M // 2). Returns (P, kmean, nmodes): per bin the mean P over
+    its modes, their mean |k|, and their count.
+    """
+    rho = np.asarray(rho, dtype=np.float64)
+    M = rho.shape[0]
+    assert rho.shape == (M, M, M)
+    if nbins is None:
+        nbins = M // 2
+    delta = rho / rho.mean() - 1.0
+    dk = np.fft.fftn(delta) / M ** 3
+    p = float(L) ** 3 * np.abs(dk) ** 2
+    n = np.fft.fftfreq(M, d=1.0 / M)
+    nz, ny, nx = np.meshgrid(n, n, n, indexing="ij")
+    nn = np.sqrt(nx * nx + ny * ny + nz * nz)
+    b = np.floor(nn + 0.5).astype(np.int64)
+    sel = (b >= 1) & (b <= nbins)
+    cnt = np.bincount(b[sel], minlength=nbins + 1)[1:]
+    psum = np.bincount(b[sel], weights=p[sel], minlength=nbins + 1)[1:]
+    ksum = np.bincount(b[sel], weights=nn[sel], minlength=nbins + 1)[1:]
+    with np.errstate(invalid="ignore", divide="ignore"):
+        P = np.where(cnt > 0, psum / cnt, 0.0)
+        kmean = np.where(cnt > 0, 2.0 * np.pi / float(L) * ksum / cnt, 0.0)
+    return P, kmean, cnt

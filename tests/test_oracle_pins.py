@@ -411,3 +411,65 @@ def test_deposit_conserves_mass_and_is_uniform_at_the_solution():
         assert abs(rho.sum() * (L / M) ** 3 - nu.sum()) < 1e-12 * L ** 3
     psi_s, _ = O.solve(y, nu, L, tol=1e-12)
     np.testing.assert_allclose(O.deposit(y, psi_s, L, M, 0.0), 1.0, rtol=0, atol=1e-10)
+
+
+# --- power spectrum of a mesh (the estimator behind d(k), Sec. "BAO reconstruction") ---
+
+def test_power_spectrum_parseval():
+    # with every mode binned, sum_b nmodes_b P_b / L^3 = mean(delta^2) (Parseval)
+    rng = np.random.default_rng(21)
+    M, L = 8, 3.0
+    rho = 1.0 + 0.1 * rng.standard_normal((M, M, M))
+    P, _, cnt = O.power_spectrum(rho, L, nbins=8)
+    delta = rho / rho.mean() - 1.0
+    assert cnt.sum() == M ** 3 - 1
+    assert abs((cnt * P).sum() / L ** 3 - (delta * delta).mean()) <= 1e-14
+
+
+def test_power_spectrum_brute_force_dft():
+    # explicit sums over the mesh points for every mode of a 4^3 mesh
+    rng = np.random.default_rng(22)
+    M, L = 4, 2.0
+    rho = 1.0 + 0.2 * rng.uniform(-1, 1, (M, M, M))
+    delta = rho / rho.mean() - 1.0
+    n1 = [0, 1, -2, -1]
+    psum = np.zeros(5)
+    cnt = np.zeros(5, dtype=int)
+    ksum = np.zeros(5)
+    for nz in n1:
+        for ny in n1:
+            for nx in n1:
+                s = 0j
+                for z in range(M):
+                    for y in range(M):
+                        for x in range(M):
+                            s += delta[z, y, x] * np.exp(-2j * np.pi * (nx * x + ny * y + nz * z) / M)
+                nn = np.sqrt(nx * nx + ny * ny + nz * nz)
+                b = int(np.floor(nn + 0.5))
+                if 1 <= b <= 4:
+                    psum[b] += L ** 3 * abs(s / M ** 3) ** 2
+                    cnt[b] += 1
+                    ksum[b] += 2 * np.pi / L * nn
+    P, k, c = O.power_spectrum(rho, L, nbins=4)
+    np.testing.assert_array_equal(c, cnt[1:])
+    assert cnt[4] == 0 and P[3] == 0.0  # |n| <= sqrt(12) < 3.5 on a 4^3 mesh
+    np.testing.assert_allclose(P[:3], psum[1:4] / cnt[1:4], rtol=1e-12)
+    np.testing.assert_allclose(k[:3], ksum[1:4] / cnt[1:4], rtol=1e-14)
+
+
+def test_power_spectrum_plane_wave():
+    # delta = A cos(2 pi 3 x / L): the two modes +-(3, 0, 0) hold (A/2)^2 each, nothing else
+    M, L, A = 16, 5.0, 0.3
+    x = (np.arange(M) + 0.5) * L / M
+    rho = np.broadcast_to(1.0 + A * np.cos(2 * np.pi * 3 * x / L), (M, M, M)).copy()
+    P, _, cnt = O.power_spectrum(rho, L)
+    expect = np.zeros(M // 2)
+    expect[2] = 2 * L ** 3 * (A / 2) ** 2 / cnt[2]
+    np.testing.assert_allclose(P, expect, rtol=1e-12, atol=1e-25)
+
+
+def test_power_spectrum_bin_counts():
+    # bin b holds the lattice points n with b - 1/2 <= |n| < b + 1/2: bin 1 is |n|^2 in
+    # {1, 2} (6 + 12 points), bin 2 is |n|^2 in {3, 4, 5, 6} (8 + 6 + 24 + 24)
+    _, _, cnt = O.power_spectrum(np.ones((8, 8, 8)) + 1e-3, 1.0)
+    assert cnt[0] == 18 and cnt[1] == 62
