@@ -48,51 +48,131 @@ __device__ __forceinline__ double sym_value(const int32_t* __restrict__ fcnt,
     return seen ? 0.5 * (cij + cji) : 0.0;
 }
 
+// Row i's facets, one per lane (rows of at most 32 facets): the symmetrised
+// coefficient of each first occurrence of a column (sym_value's value, with the same
+// sums in the same order, so L stays exactly symmetric) and whether it enters L.
+struct RowSym {
+    int32_t j;
+    double v;
+    bool keep;
+};
+
+__device__ __forceinline__ RowSym row_sym_warp(const int32_t* __restrict__ fcnt,
+                                               const int32_t* __restrict__ fcol,
+                                               const double* __restrict__ fval, int64_t i,
+                                               int n, int lane) {
+    RowSym r;
+    const bool act = lane < n;
+    r.j = act ? fcol[i * FCAP + lane] : -1;
+    const double f = act ? fval[i * FCAP + lane] : 0.0;
+    // lanes holding the same column; inactive lanes get keys of their own
+    const uint32_t mm = __match_any_sync(FULLMASK, act ? (uint32_t)r.j : 0x80000000u | lane);
+    const bool first = act && (__ffs(mm) - 1) == lane;
+    // i's reports of j, summed in slot order from the first occurrence (as sym_value)
+    double cij = 0.0 + f;
+    if (__any_sync(FULLMASK, __popc(mm) > 1)) {
+        cij = 0.0;
+        for (int src = 0; src < 32; src++) {
+            const double fs = __shfl_sync(FULLMASK, f, src);
+            if ((mm >> src) & 1u) cij += fs;
+        }
+    }
+    double cji = 0.0;
+    bool seen = false;
+    if (first) {
+        const int nj = fcnt[r.j];
+        for (int u = 0; u < nj; u++)
+            if (fcol[(int64_t)r.j * FCAP + u] == (int32_t)i) {
+                cji += fval[(int64_t)r.j * FCAP + u];
+                seen = true;
+            }
+    }
+    r.v = (first && seen) ? 0.5 * (cij + cji) : 0.0;
+    r.keep = r.v > 0.0;
+    return r;
+}
+
+// one warp per row: the row's entry count (kept facets + the diagonal)
 __global__ void csr_count_kernel(const int32_t* __restrict__ fcnt, const int32_t* __restrict__ fcol,
                                  const double* __restrict__ fval, int64_t N,
                                  int32_t* __restrict__ rowcnt) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (i >= N) return;
-    int n = fcnt[i], kept = 0;
-    for (int t = 0; t < n; t++)
-        if (sym_value(fcnt, fcol, fval, i, t) > 0.0) kept++;
-    rowcnt[i] = kept + 1;
+    const int n = fcnt[i];
+    if (n > 32) {  // rare: the row in lane 0, serially
+        if (lane == 0) {
+            int kept = 0;
+            for (int t = 0; t < n; t++)
+                if (sym_value(fcnt, fcol, fval, i, t) > 0.0) kept++;
+            rowcnt[i] = kept + 1;
+        }
+        return;
+    }
+    const RowSym r = row_sym_warp(fcnt, fcol, fval, i, n, lane);
+    const uint32_t km = __ballot_sync(FULLMASK, r.keep);
+    if (lane == 0) rowcnt[i] = __popc(km) + 1;
 }
 
+// one warp per row: the diagonal first, then the kept entries in increasing column
+// (each lane's rank among them), values -c_ij; the diagonal is their warp sum
 __global__ void csr_fill_kernel(const int32_t* __restrict__ fcnt, const int32_t* __restrict__ fcol,
                                 const double* __restrict__ fval, int64_t N,
                                 const int64_t* __restrict__ row_ptr, int32_t* __restrict__ col,
                                 double* __restrict__ val, double* __restrict__ dinv) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (i >= N) return;
-    int n = fcnt[i];
-    int64_t p0 = row_ptr[i];
-    int64_t p = p0 + 1;
-    double diag = 0.0;
-    for (int t = 0; t < n; t++) {
-        double v = sym_value(fcnt, fcol, fval, i, t);
-        if (!(v > 0.0)) continue;
-        int32_t j = fcol[i * FCAP + t];
-        // insertion into the row, increasing column
-        int64_t q = p;
-        while (q > p0 + 1 && col[q - 1] > j) {
-            col[q] = col[q - 1];
-            val[q] = val[q - 1];
-            q--;
+    const int n = fcnt[i];
+    const int64_t p0 = row_ptr[i];
+    if (n > 32) {  // rare: the row in lane 0, serially (insertion by column)
+        if (lane == 0) {
+            int64_t p = p0 + 1;
+            double diag = 0.0;
+            for (int t = 0; t < n; t++) {
+                const double v = sym_value(fcnt, fcol, fval, i, t);
+                if (!(v > 0.0)) continue;
+                const int32_t j = fcol[i * FCAP + t];
+                int64_t q = p;
+                while (q > p0 + 1 && col[q - 1] > j) {
+                    col[q] = col[q - 1];
+                    val[q] = val[q - 1];
+                    q--;
+                }
+                col[q] = j;
+                val[q] = -v;
+                p++;
+                diag += v;
+            }
+            col[p0] = (int32_t)i;
+            val[p0] = diag;
+            dinv[i] = diag > 0.0 ? 1.0 / diag : 0.0;
         }
-        col[q] = j;
-        val[q] = -v;
-        p++;
-        diag += v;
+        return;
     }
-    col[p0] = (int32_t)i;
-    val[p0] = diag;
-    dinv[i] = diag > 0.0 ? 1.0 / diag : 0.0;
+    const RowSym r = row_sym_warp(fcnt, fcol, fval, i, n, lane);
+    const uint32_t km = __ballot_sync(FULLMASK, r.keep);
+    int rank = 0;
+    for (int src = 0; src < 32; src++) {
+        const int32_t js = __shfl_sync(FULLMASK, r.j, src);
+        if (((km >> src) & 1u) && js < r.j) rank++;
+    }
+    if (r.keep) {
+        col[p0 + 1 + rank] = r.j;
+        val[p0 + 1 + rank] = -r.v;
+    }
+    double diag = r.keep ? r.v : 0.0;
+    for (int o = 16; o > 0; o >>= 1) diag += __shfl_xor_sync(FULLMASK, diag, o);
+    if (lane == 0) {
+        col[p0] = (int32_t)i;
+        val[p0] = diag;
+        dinv[i] = diag > 0.0 ? 1.0 / diag : 0.0;
+    }
 }
 
 int csr_count(DeviceState& d, int64_t* nnz_out, cudaStream_t s) {
     const int64_t N = d.N;
-    unsigned nb = (unsigned)((N + 255) / 256);
+    unsigned nb = (unsigned)((N + 7) / 8);  // 8 rows (warps) per block
     csr_count_kernel<<<nb, 256, 0, s>>>(d.fcnt, d.fcol, d.fval, N, d.rowcnt);
     note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
@@ -109,7 +189,7 @@ int csr_count(DeviceState& d, int64_t* nnz_out, cudaStream_t s) {
 
 int csr_fill(DeviceState& d, cudaStream_t s) {
     const int64_t N = d.N;
-    unsigned nb = (unsigned)((N + 255) / 256);
+    unsigned nb = (unsigned)((N + 7) / 8);  // 8 rows (warps) per block
     csr_fill_kernel<<<nb, 256, 0, s>>>(d.fcnt, d.fcol, d.fval, N, d.row_ptr, d.col, d.val, d.dinv);
     note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
@@ -124,29 +204,52 @@ __global__ void csr_user_count(const int64_t* __restrict__ row_ptr, const int32_
     cnt_user[perm[s]] = (int32_t)(row_ptr[s + 1] - row_ptr[s]);
 }
 
+// one warp per sorted row s: row perm[s] of the caller's matrix, the diagonal first and
+// the off-diagonal entries ranked by their caller-order column
 __global__ void csr_user_fill(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                               const double* __restrict__ val, const int32_t* __restrict__ perm,
                               int64_t N, const int64_t* __restrict__ rp_u,
                               int32_t* __restrict__ col_u, double* __restrict__ val_u) {
-    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (s >= N) return;
-    int64_t b = row_ptr[s], e = row_ptr[s + 1];
-    int64_t o = rp_u[perm[s]];
-    col_u[o] = perm[col[b]];
-    val_u[o] = val[b];
-    int64_t p = o + 1;
-    for (int64_t t = b + 1; t < e; t++) {
-        int32_t j = perm[col[t]];
-        double v = val[t];
-        int64_t q = p;
-        while (q > o + 1 && col_u[q - 1] > j) {
-            col_u[q] = col_u[q - 1];
-            val_u[q] = val_u[q - 1];
-            q--;
+    const int64_t b = row_ptr[s], e = row_ptr[s + 1];
+    const int64_t o = rp_u[perm[s]];
+    const int m = (int)(e - b) - 1;  // off-diagonal entries
+    if (lane == 0) {
+        col_u[o] = perm[col[b]];
+        val_u[o] = val[b];
+    }
+    if (m > 32) {  // rare: lane 0, insertion by column
+        if (lane == 0) {
+            int64_t p = o + 1;
+            for (int64_t t = b + 1; t < e; t++) {
+                const int32_t j = perm[col[t]];
+                const double v = val[t];
+                int64_t q = p;
+                while (q > o + 1 && col_u[q - 1] > j) {
+                    col_u[q] = col_u[q - 1];
+                    val_u[q] = val_u[q - 1];
+                    q--;
+                }
+                col_u[q] = j;
+                val_u[q] = v;
+                p++;
+            }
         }
-        col_u[q] = j;
-        val_u[q] = v;
-        p++;
+        return;
+    }
+    const bool act = lane < m;
+    const int32_t j = act ? perm[col[b + 1 + lane]] : 0;
+    const double v = act ? val[b + 1 + lane] : 0.0;
+    int rank = 0;
+    for (int src = 0; src < 32; src++) {
+        const int32_t js = __shfl_sync(FULLMASK, j, src);
+        if (src < m && js < j) rank++;
+    }
+    if (act) {
+        col_u[o + 1 + rank] = j;
+        val_u[o + 1 + rank] = v;
     }
 }
 
@@ -160,8 +263,8 @@ int assemble_csr_user(DeviceState& d, int64_t nnz, cudaStream_t s) {
     SDOT_CUDA_TRY(cudaMemsetAsync(d.rowcnt + N, 0, 4, s));
     int rc = scan_exclusive_i32_to_i64(d.rowcnt, d.row_ptr_u, N + 1, d.partials + 65536, s);
     if (rc) return rc;
-    csr_user_fill<<<nb, 256, 0, s>>>(d.row_ptr, d.col, d.val, d.perm, N, d.row_ptr_u, d.col_u,
-                                     d.val_u);
+    csr_user_fill<<<(unsigned)((N + 7) / 8), 256, 0, s>>>(d.row_ptr, d.col, d.val, d.perm, N,
+                                                         d.row_ptr_u, d.col_u, d.val_u);
                                      note_launch();
     SDOT_CUDA_TRY(cudaGetLastError());
     return SDOT_OK;
