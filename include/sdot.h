@@ -245,6 +245,29 @@ int sdot_knn_static(const double* pos, int64_t N, const double box[3], int k, in
                     void* stream);
 
 /*
+ * Power spectrum of a density mesh: the estimator of the fractional BAO signal
+ * d(k) = P_wig(k) / P_nw(k) - 1 that compares the densities reconstructed (sdot_mesh)
+ * from a wiggle / no-wiggle pair (Sec. "BAO reconstruction", Fig. 2).
+ *  rho:    M^3 doubles (host or device), indexed (z M + y) M + x like sdot_mesh's, of a
+ *          periodic cubic box of side L; its mean must be positive.
+ *  M:      2 ... 1024.   L: the box side (> 0).
+ *  nbins:  1 ... 2 M bins; bin b = 1 ... nbins holds the modes k = 2 pi n / L with
+ *          b - 1/2 <= |n| < b + 1/2 (n integer, every mode of the full transform once).
+ *  P:      nbins doubles out (host): the mean over the bin's modes of L^3 |delta_k|^2,
+ *          delta = rho / mean(rho) - 1, delta_k its discrete transform divided by M^3.
+ *  kmean:  nbins doubles out (host) or NULL: the mean |k| of the bin's modes.
+ *  nmodes: nbins int64 out (host) or NULL: the bin's mode count.
+ *  stream: cudaStream_t (NULL: legacy default stream); the call returns after
+ *          synchronising it.
+ * The transform is cuFFT's (loaded on first use; SDOT_ERR_CUDA with a message if it
+ * cannot be); the per-bin sums are 64-bit fixed point (unit 2^-38 of the bin's largest
+ * |delta_k|^2), so the result is reproducible and within ~1e-10 relative of the exact
+ * mean. Device scratch of about 3 M^3 doubles is allocated and freed by the call.
+ */
+int sdot_power_spectrum(const double* rho, int M, double L, int nbins, double* P,
+                        double* kmean, int64_t* nmodes, void* stream);
+
+/*
  * After the solve: the Kantorovich potential at tau_I on a mesh and the mass density of
  * the cells moved to an intermediate time (Sec. "Monge-Ampere-Kantorovich
  * Reconstruction": the Legendre transform of psi, and the last paragraph; Fig. 1).

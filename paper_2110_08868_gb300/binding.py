@@ -96,6 +96,7 @@ EXPORTS = ["sdot_default_options", "sdot_create", "sdot_set_stream", "sdot_set_a
            "sdot_laguerre",
            "sdot_solve", "sdot_csr_copy", "sdot_get_psi", "sdot_displacement", "sdot_knn",
            "sdot_cell_status", "sdot_knn_static", "sdot_last_eval", "sdot_mesh", "sdot_size",
+           "sdot_power_spectrum",
            "sdot_destroy",
            "sdot_kernel_launches", "sdot_last_error",
            "sdot_server_default_options", "sdot_server_footprint", "sdot_server_create",
@@ -141,6 +142,7 @@ def load(path=LIB_PATH):
     lib.sdot_size.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I)]
     lib.sdot_last_eval.argtypes = [P, ctypes.POINTER(sdot_eval_info)]
     lib.sdot_mesh.argtypes = [P, D, I, P, P, P]
+    lib.sdot_power_spectrum.argtypes = [P, I, D, I, P, P, P, P]
     lib.sdot_destroy.argtypes = [P]
     lib.sdot_destroy.restype = None
     lib.sdot_kernel_launches.argtypes = []
@@ -297,6 +299,28 @@ def sdot_knn_static(pos, box, k, nbr, stream=None):
 def sdot_mesh(ctx, lam, mesh, rho=None, phi=None, owner=None):
     return load().sdot_mesh(ctx, float(lam), int(mesh), _ptr(rho), _ptr(phi),
                             _ptr(owner, np.int32))
+
+
+def sdot_power_spectrum(rho, L, nbins=None, stream=None):
+    """Power spectrum of an M^3 density mesh of a cubic box of side L (host array or
+    CUDA tensor, indexed [z, y, x]; see include/sdot.h). Returns (P, kmean, nmodes) per
+    bin."""
+    M = int(rho.shape[0])
+    if tuple(rho.shape) != (M, M, M):
+        raise ValueError("rho must be an M x M x M mesh")
+    if hasattr(rho, "is_contiguous"):
+        if rho.dtype != __import__("torch").float64 or not rho.is_contiguous():
+            raise ValueError("rho must be a contiguous float64 tensor")
+    else:
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+    nb = M // 2 if nbins is None else int(nbins)
+    P = np.zeros(nb)
+    k = np.zeros(nb)
+    n = np.zeros(nb, dtype=np.int64)
+    h = getattr(stream, "cuda_stream", stream)
+    check(load().sdot_power_spectrum(_ptr(rho), M, float(L), nb, _ptr(P), _ptr(k),
+                                     _ptr(n, np.int64), ctypes.c_void_p(h) if h else None))
+    return P, k, n
 
 
 def sdot_last_eval(ctx, info):

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsdot.so")
 SOURCES = ["grid_knn.cu", "clip.cu", "linalg.cu", "api.cu", "static_knn.cu", "serve.cu",
-           "mesh.cu"]
+           "mesh.cu", "spectrum.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -64,7 +64,7 @@ def build(verbose=False, force=False, extra=()):
         list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + ".tmp"
-        run([nvcc()] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs)
+        run([nvcc()] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs + ["-ldl"])
         os.replace(tmp, LIB)
     return LIB
 
