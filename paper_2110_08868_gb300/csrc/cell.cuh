@@ -1694,6 +1694,9 @@ __device__ __forceinline__ bool process_cell(Poly<R, C>& P, const ClipParams& cp
     // a certifying first pass carries the cell's security certificate between
     // evaluations (see CERT_EPS): used when it still holds, recorded after a walk
     const bool rec = MODE == MODE_CERTIFY && cp.pass == 1 && cp.cert_use;
+    // the FP64 re-clip of a cell the FP32 check sent there uses the certificate the
+    // first pass kept for it, checked against the FP64 polytope
+    const bool use3 = MODE == MODE_FULL && !BIG && cp.pass == 3 && cp.cert_use;
     bool carried = false, stored = false, reframed = false;
     int ncert = -1;
     if (!st) {
@@ -1704,7 +1707,7 @@ __device__ __forceinline__ bool process_cell(Poly<R, C>& P, const ClipParams& cp
         }
         b.psi_i = cc.si.phi;
         poly_bounds(P, cp, b, lane);
-        if (rec && warm) {
+        if ((rec || use3) && warm) {
             const int nc = cp.cert_n[i];
             if (nc != 0xff) carried = cert_check(P, cp, cc, b, i, nc, lane);
         }
@@ -1813,12 +1816,16 @@ __device__ __forceinline__ bool process_cell(Poly<R, C>& P, const ClipParams& cp
             cp.q64_out[q] = (int32_t)i;
         }
         // the certificate stays valid only for a clean cell whose every plane other
-        // than the box's is a facet (the planes of its next warm start)
-        const bool clean = rec && st == 0 && !reframed && cp.fcnt[i] == P.np - 6;
-        if (!clean || !(carried || stored)) cp.cert_n[i] = 0xff;
-        else if (stored) cp.cert_n[i] = (uint8_t)ncert;
+        // than the box's is a facet (the planes of its next warm start); a first-pass
+        // cell whose only failure is the FP32 check keeps it for its FP64 re-clip
+        const bool facets = !reframed && cp.fcnt[i] == P.np - 6;
+        const bool keep1 = rec && facets && (carried || stored) &&
+                           (st == 0 || (redo && st == CS_INCONSISTENT));
+        const bool keep3 = use3 && facets && carried && st == 0;
+        if (!(keep1 || keep3)) cp.cert_n[i] = 0xff;
+        else if (keep1 && stored) cp.cert_n[i] = (uint8_t)ncert;
     }
-    return carried;
+    return rec && carried;
 }
 
 }  // namespace sdot
