@@ -196,3 +196,17 @@ def test_knn_static_wrapper_rejects_bad_buffers(pos_shape, nbr_shape, k, devs, m
 def test_knn_static_wrapper_rejects_host_buffers():
     with pytest.raises(ValueError, match="CUDA tensor"):
         B.sdot_knn_static(_pos(100), [1.0] * 3, 8, np.zeros((100, 8), np.int32))
+
+
+def test_power_spectrum_argument_checks_need_no_gpu():
+    # sdot_power_spectrum refuses bad arguments before touching the device
+    rho = np.ones((8, 8, 8))
+    for L, nbins in ((0.0, 4), (-1.0, 4), (np.inf, 4), (np.nan, 4), (1.0, 0), (1.0, 17)):
+        with pytest.raises(B.SdotError) as e:
+            B.sdot_power_spectrum(rho, L, nbins)
+        assert e.value.code == B.SDOT_ERR_ARG
+        assert "sdot_power_spectrum" in B.sdot_last_error()
+    with pytest.raises(B.SdotError):
+        B.sdot_power_spectrum(np.ones((1, 1, 1)), 1.0, 1)  # M < 2
+    with pytest.raises(ValueError):
+        B.sdot_power_spectrum(np.ones((8, 8, 4)), 1.0, 4)  # not a cube
