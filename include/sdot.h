@@ -179,7 +179,10 @@ int sdot_laguerre(sdot_ctx* ctx, const double* psi, double* volumes, double* cen
  * Damped Newton maximisation of K (concave and C^2, Sec. "Monge-Ampere-Kantorovich
  * Reconstruction") from psi0 (N doubles; NULL: 0) until
  * max_j |V_j - nu_j| / nu_j <= tol. Each step solves L delta = nu - V by
- * Jacobi-preconditioned CG and takes the first alpha in a0, a0/2, a0/4, ... with
+ * Jacobi-preconditioned CG to opt.cg_rtol (L in sliced-ELL form with FP32 weights and
+ * FP32 arithmetic per stored entry, vectors and dot products in FP64: the direction is
+ * an inexact solve, and the precision of the answer is that of the evaluations, which
+ * decide every step) and takes the first alpha in a0, a0/2, a0/4, ... with
  * min_j V_j >= eps0 and ||nu - V||_2 <= (1 - alpha/2) ||nu - V(psi)||_2, where
  * eps0 = 1/2 min(min_j V_j(psi0), min_j nu_j); a0 = 1, or min(1, 4 alpha_prev) after
  * the first step when opt.warm_alpha is set. In mixed precision, when the error is
