@@ -10,7 +10,14 @@ step time, summed over ranks. Positions and weights are in device memory when th
 region starts; ``e2e`` repeats the calls through host buffers (psi in, volumes and
 centroids out, copied inside the timed region). ``extra.ot_solve_s`` holds the OT solve
 time from psi = 0 (sdot_create + sdot_solve to tol) in both precisions, measured in the
-same run.
+same run. Every timed call certifies every cell, by its security walk or by the
+certificate carried from the previous call when psi and the cell moved less than its
+reserves; ``extra.eval_detail.carried`` counts the carried cells, and
+``extra.cells_per_s_walk_only`` times the same calls on a context with carrying off.
+``roofline`` is the first clipping pass against the derived FP32 peak, and
+``extra.roofline_cg`` is the CG iteration against the measured HBM bandwidth. Their
+``traffic`` fields are DRAM bytes from ncu captures of the current kernels on the 128^3
+version of the box, scaled to a launch.
 The default workload is the 256^3 Zel'dovich box with 5% clumped points (17.6 M
 seeds), mixed precision. ``--impl reference`` times the CPU oracle instead on a
 bounded sample of the same workload (certified cells at psi = 0, cells/s).
